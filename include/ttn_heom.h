@@ -1,0 +1,206 @@
+/*
+ * ttn_heom.h -- C ABI of the GB300 (sm_103a) TTN-HEOM propagation library.
+ *
+ * The library propagates the extended density operator (EDO) of the bexcitonic
+ * HEOM (TENSO paper, Sec. 2.2, Eq. heom-std) stored as a tree tensor network
+ * (Sec. 2.3, Eq. omega_tensor) under a sum-of-products (SOP) generator
+ * (Eq. master_lvn), with the fixed-rank (ps1) and adaptive-rank (ps2)
+ * projector-splitting integrators (Sec. 2.3, last paragraph), and returns the
+ * reduced density matrix rho_S = <0|Omega> (Sec. 2.2).
+ *
+ * Conventions shared by every entry point
+ *  - Complex numbers are two consecutive doubles (real, imaginary).
+ *  - Matrices are row-major. An operator acting on a leg of dimension d is a
+ *    d x d matrix M that maps amplitude index a to a': new[a'] = sum_a M[a'][a] old[a].
+ *  - Legs: leg 0 = system ket index i, leg 1 = system bra index j, legs 2.. =
+ *    Fock legs of the bath features (Eq. EDO-elements). Legs 0 and 1 must sit
+ *    on the root node 0. A right multiplication B A^dagger of the system density
+ *    matrix acts on leg 1 with the matrix conj(A) (Sec. 2.2, A^< B = B A^dagger).
+ *  - Node tensors are stored row-major with their legs in canonical order:
+ *    the parent bond first (absent at the root), then the child nodes and
+ *    open legs sorted by the smallest open-leg index below them. Only nodes
+ *    with exactly three legs are supported (tensor trains and binary trees).
+ *  - Ownership: every host array passed in is read during the call and never
+ *    retained. Device memory is one caller-provided workspace (see
+ *    ttn_workspace_size / ttn_set_workspace); the library allocates no device
+ *    memory itself. The caller frees the workspace after ttn_destroy.
+ *  - Errors: every entry point returns a ttn_status and never aborts;
+ *    ttn_last_error(h) describes the last failure. A failing call leaves the
+ *    handle in the state it had before the call, except that TTN_ENUMERIC and
+ *    TTN_ECUDA from ttn_step leave the state undefined (re-seed with
+ *    ttn_set_rdo0 or ttn_set_node).
+ *  - A handle is not thread safe; distinct handles are independent.
+ *  - All device work is issued on the stream given by ttn_set_stream
+ *    (default: the legacy default stream). Calls that return host data
+ *    (ttn_rdm, ttn_get_node) synchronise that stream.
+ */
+#ifndef TTN_HEOM_H
+#define TTN_HEOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ttn_ctx* ttn_t;
+
+typedef enum {
+  TTN_OK = 0,
+  TTN_EINVAL = 1,        /* bad argument (tree, dims, ranks, operator, size) */
+  TTN_ENOMEM = 2,        /* workspace too small or not set */
+  TTN_ECUDA = 3,         /* a CUDA call failed (message in ttn_last_error) */
+  TTN_ENUMERIC = 4,      /* non-finite value detected in the state */
+  TTN_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+  TTN_ESTATE = 6,        /* call out of order (e.g. ttn_step before sop_load) */
+  TTN_EUNSUPPORTED = 7   /* valid request this build does not implement */
+} ttn_status;
+
+/* Arithmetic of the node and bond contractions. QR, SVD, RK4 stage
+ * accumulation and the reduced density matrix are FP64 in every mode. */
+enum { TTN_FP64 = 0, TTN_MIXED_FP32 = 1 };
+
+/* Propagation schemes (Sec. 2.3): ps1 fixed rank, ps2 adaptive rank.
+ * vmf (direct integration) is not implemented: TTN_EUNSUPPORTED. */
+enum { TTN_PS1 = 1, TTN_PS2 = 2, TTN_VMF = 3 };
+
+/* Tree topology: parent[0] = -1 (node 0 is the root), parent[u] in [0, n_nodes)
+ * otherwise; leg_node[l] = node carrying open leg l. */
+typedef struct {
+  int32_t n_nodes;
+  const int32_t* parent;
+  int32_t n_legs;
+  const int32_t* leg_node;
+} ttn_tree;
+
+/* Numerical parameters (defaults in parentheses).
+ *  qr_tol    (1e-12) Householder QR treats a column whose remaining norm is at
+ *                    most qr_tol*||A||_F as exactly dependent: no reflector,
+ *                    R_jj = 0, Q column = H_0..H_{j-1} e_j.
+ *  kappa     (2.5)   RK4 substeps per flow of length tau:
+ *                    m = max(1, ceil(|tau| * Lambda / kappa - 1e-9)), Lambda =
+ *                    sum over terms of |coef| * prod ||op||_2 (|coef| * g_bound
+ *                    for driven terms), fixed at sop_load.
+ *  ps2_atol  (1e-7)  ps2 keeps r0 = #{sigma > ps2_atol} ... (Sec. 5.3, Table 4)
+ *  ps2_ratio (2)     ... and then min(cap, max(1, ceil(ps2_ratio * r0))) values.
+ *  max_rank  (32)    ps2 bond-rank cap (Sec. 5.3, max_auxiliary_rank).
+ *  svd_tol   (1e-12) kept singular values <= svd_tol*sigma_1 are replaced by a
+ *                    deterministic completion with zero weight. */
+typedef struct {
+  double qr_tol;
+  double kappa;
+  double ps2_atol;
+  double ps2_ratio;
+  int32_t max_rank;
+  double svd_tol;
+} ttn_params;
+
+/* Create a handle (Sec. 2.3, Eq. omega_tensor). leg_dims[n_legs]: leg
+ * dimensions (leg 0 and 1 both M). ranks[n_nodes]: requested rank of the bond
+ * between node u and its parent (ranks[0] ignored); each is capped to the
+ * product of the other leg dimensions at either end node, iterated to a fixed
+ * point (ttn_get_ranks reports the result). precision: TTN_FP64 or
+ * TTN_MIXED_FP32. Returns TTN_EINVAL for a parent array that is not a tree
+ * rooted at 0, legs 0/1 not on the root, a node without three legs, dims < 1,
+ * ranks < 1. Host-only: no device work. */
+ttn_status ttn_create(const ttn_tree* tree, const int32_t* leg_dims, const int32_t* ranks,
+                      int32_t precision, ttn_t* out);
+
+/* Set numerical parameters; may be called any time before ttn_set_workspace
+ * (max_rank changes the workspace size for ps2). */
+ttn_status ttn_set_params(ttn_t h, const ttn_params* p);
+ttn_status ttn_get_params(ttn_t h, ttn_params* p);
+
+/* Load the SOP generator of Eq. master_lvn:
+ *     L(t) = sum_m coef_m * g_{d_m}(t) * prod_{f in term m} op_f on leg(op_f).
+ * Local operators: op k acts on leg op_leg[k] with d = leg_dims[op_leg[k]]; its
+ * d*d complex entries start at op_data[2*op_offset[k]] (offsets in complex
+ * elements). Terms: term m uses ops term_ops[term_offsets[m] .. term_offsets[m+1]-1]
+ * (at most two, on distinct legs); coef[2m], coef[2m+1] its complex
+ * coefficient; coef_drive[m] = -1 (static) or a drive id >= 0 whose g(t)
+ * multiplies the coefficient (driven terms may only act on legs of the root).
+ * Terms are merged on the host into per-bond operator classes (single-leg sums
+ * and two-leg groups keyed by their more shared factor). Host-only.
+ * Errors: TTN_EINVAL (bad leg, dims, op id, more than two factors, repeated
+ * leg in one term, non-finite entry), TTN_EUNSUPPORTED (driven term off the root). */
+ttn_status sop_load(ttn_t h, int32_t n_ops, const int32_t* op_leg, const int64_t* op_offset,
+                    const double* op_data, int32_t n_terms, const int32_t* term_offsets,
+                    const int32_t* term_ops, const double* coef, const int32_t* coef_drive);
+
+/* Drive d: g(t, user) is sampled on the host at the half-step midpoints
+ * t0 + dt/4 and t0 + 3dt/4 of every step (the driven system term is frozen
+ * during each half sweep); g_bound >= max |g| enters Lambda. Must precede
+ * ttn_set_workspace. */
+typedef double (*ttn_drive_fn)(double t, void* user);
+ttn_status ttn_set_drive(ttn_t h, int32_t id, ttn_drive_fn g, void* user, double g_bound);
+
+/* Device workspace: bytes needed for the state, environments, operators and
+ * scratch (sized for the rank caps). Valid after sop_load. */
+ttn_status ttn_workspace_size(ttn_t h, size_t* bytes);
+/* Bind a device buffer of at least ttn_workspace_size bytes, 256-byte aligned,
+ * on the current CUDA device. Uploads operators, builds the initial product
+ * state rho0 = |0><0| (x) |0..0> and its environments. */
+ttn_status ttn_set_workspace(ttn_t h, void* device_ptr, size_t bytes);
+/* cudaStream_t passed as void*. */
+ttn_status ttn_set_stream(ttn_t h, void* stream);
+
+/* Initial product state Omega(0) = rho0 (x) |0..0> (Sec. 2.2): root
+ * A[i,j,0] = rho0[i][j], other root entries 0; every other core
+ * U[a, flat(children)] = delta(a, flat) (the first r columns of the identity).
+ * rho0: M*M complex, row-major. Resets time to 0 and rebuilds environments. */
+ttn_status ttn_set_rdo0(ttn_t h, const double* rho0);
+
+/* Advance n_steps steps of length dt with scheme TTN_PS1 or TTN_PS2 (one step =
+ * the symmetric composition of a half sweep over dt/2 and its adjoint). The
+ * orthogonality centre is at the root before and after. Asynchronous on the
+ * handle's stream except for drive sampling on the host. TTN_ENUMERIC if a
+ * non-finite amplitude appeared (checked once per call). */
+ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps);
+
+/* rho_S = <0|Omega>: contract every feature leg with the n = 0 vector.
+ * rho_out: caller-allocated host buffer of M*M complex, row-major. Synchronises. */
+ttn_status ttn_rdm(ttn_t h, double* rho_out);
+/* Same, written asynchronously to a device buffer of M*M complex. */
+ttn_status ttn_rdm_device(ttn_t h, void* rho_dev);
+
+/* Effective bond ranks (ranks_out[n_nodes], entry 0 = 0); for ps2 the current ones. */
+ttn_status ttn_get_ranks(ttn_t h, int32_t* ranks_out);
+/* Current dims of node u's three legs in canonical order. */
+ttn_status ttn_node_shape(ttn_t h, int32_t u, int32_t* dims3);
+/* Copy node tensor u (prod(dims) complex) to / from the host. ttn_set_node
+ * requires non-root nodes to be semi-unitary toward their parent (Eq.
+ * semiunitary); environments are rebuilt before the next step. Synchronises. */
+ttn_status ttn_get_node(ttn_t h, int32_t u, double* host_out);
+ttn_status ttn_set_node(ttn_t h, int32_t u, const double* host_in);
+/* Simulation time reached (starts at 0, Sec. 5.1 checkpoint convention). */
+ttn_status ttn_time(ttn_t h, double* t);
+/* RK4 substeps used for a flow of length tau under the current generator. */
+ttn_status ttn_substeps(ttn_t h, double tau, int32_t* m);
+
+/* Propagate several independent handles (same scheme and dt) in one call.
+ * Every handle needs its own workspace and must not share a stream with
+ * another handle in the list unless it is the same stream for all. */
+ttn_status ttn_batch_step(ttn_t* hs, int32_t n, double dt, int32_t scheme, int32_t n_steps);
+
+/* Kernel accounting (instrumentation, not on the physics path). Kernel
+ * classes: 0 = node/bond application (sum of mode products with the fused RK4
+ * stage update), 1 = environment update (mode products + projection),
+ * 2 = Householder QR, 3 = everything else (absorb, copies, RDM, drive, checks).
+ * ttn_stats: launches and algorithmic FLOPs issued since the last reset
+ * (complex multiply-add = 8 FLOPs), counted on the host, always on.
+ * ttn_profile(h, 1) additionally brackets every launch with CUDA events on the
+ * handle's stream; ttn_profile_read synchronises and returns the summed device
+ * time of each class in milliseconds. ttn_stats_reset clears both. */
+ttn_status ttn_stats(ttn_t h, int32_t kind, int64_t* launches, double* flops);
+ttn_status ttn_profile(ttn_t h, int32_t on);
+ttn_status ttn_profile_read(ttn_t h, int32_t kind, double* ms);
+ttn_status ttn_stats_reset(ttn_t h);
+
+const char* ttn_last_error(ttn_t h);
+void ttn_destroy(ttn_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTN_HEOM_H */

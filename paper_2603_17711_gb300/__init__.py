@@ -1,0 +1,198 @@
+"""GB300-native TTN-HEOM propagation (TENSO method, arXiv 2603.17711).
+
+The compute path is the CUDA library ``libttnheom.so`` (C ABI in
+include/ttn_heom.h); this package only marshals arguments to it and lends it
+PyTorch device memory and streams. There is no CPU fallback: constructing a
+``TTN`` without the built library or without a CUDA device raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Callable, Optional, Sequence
+
+import numpy as np
+
+from . import heom
+from ._lib import (DRIVE_FN, TTN_FP64, TTN_MIXED_FP32, TTN_OK, TTN_PS1, TTN_PS2, TTN_VMF,
+                   TTNError, as_f64, as_i32, ptr, ttn_params, ttn_tree)
+from . import _lib
+
+__all__ = ["TTN", "TTNError", "heom", "TTN_FP64", "TTN_MIXED_FP32", "TTN_PS1", "TTN_PS2", "TTN_VMF",
+           "library", "from_model"]
+
+_LIB: Optional[C.CDLL] = None
+
+
+def library() -> C.CDLL:
+    """The loaded libttnheom.so (raises if it is not built)."""
+    global _LIB
+    if _LIB is None:
+        _LIB = _lib.load()
+    return _LIB
+
+
+class TTN:
+    """One TTN-HEOM state on the GPU; methods mirror the C ABI entry points."""
+
+    def __init__(self, parent: Sequence[int], leg_node: Sequence[int], leg_dims: Sequence[int],
+                 ranks: Sequence[int], precision: int = TTN_FP64):
+        self.lib = library()
+        self._parent = as_i32(parent)
+        self._leg_node = as_i32(leg_node)
+        self.leg_dims = as_i32(leg_dims)
+        self.M = int(self.leg_dims[0])
+        tree = ttn_tree(len(self._parent), ptr(self._parent, C.c_int32), len(self._leg_node),
+                        ptr(self._leg_node, C.c_int32))
+        h = C.c_void_p()
+        st = self.lib.ttn_create(C.byref(tree), ptr(self.leg_dims, C.c_int32), ptr(as_i32(ranks), C.c_int32),
+                                 precision, C.byref(h))
+        if st != TTN_OK:
+            raise TTNError(st, "ttn_create")
+        self.h = h
+        self.n_nodes = len(self._parent)
+        self._drive_cbs = []
+        self._ws = None
+
+    # -- plumbing -----------------------------------------------------------
+    def _check(self, st: int, what: str) -> None:
+        if st != TTN_OK:
+            msg = self.lib.ttn_last_error(self.h)
+            raise TTNError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.ttn_destroy(self.h)
+            self.h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points -------------------------------------------------------
+    def ttn_set_params(self, **kw) -> None:
+        p = ttn_params()
+        self._check(self.lib.ttn_get_params(self.h, C.byref(p)), "ttn_get_params")
+        for k, v in kw.items():
+            setattr(p, k, v)
+        self._check(self.lib.ttn_set_params(self.h, C.byref(p)), "ttn_set_params")
+
+    def sop_load(self, arrays: dict) -> None:
+        a = {k: np.ascontiguousarray(v) for k, v in arrays.items()}
+        self._sop = a
+        n_ops = len(a["op_leg"])
+        n_terms = len(a["term_offsets"]) - 1
+        self._check(self.lib.sop_load(self.h, n_ops, ptr(as_i32(a["op_leg"]), C.c_int32),
+                                      ptr(a["op_offset"].astype(np.int64), C.c_int64),
+                                      ptr(as_f64(a["op_data"]), C.c_double), n_terms,
+                                      ptr(as_i32(a["term_offsets"]), C.c_int32),
+                                      ptr(as_i32(a["term_ops"]), C.c_int32),
+                                      ptr(as_f64(a["coef"]), C.c_double),
+                                      ptr(as_i32(a["coef_drive"]), C.c_int32)), "sop_load")
+
+    def ttn_set_drive(self, drive_id: int, g: Callable[[float], float], bound: float) -> None:
+        cb = DRIVE_FN(lambda t, _u: float(g(t)))
+        self._drive_cbs.append(cb)  # keep the trampoline alive
+        self._check(self.lib.ttn_set_drive(self.h, drive_id, cb, None, float(bound)), "ttn_set_drive")
+
+    def ttn_workspace_size(self) -> int:
+        n = C.c_size_t()
+        self._check(self.lib.ttn_workspace_size(self.h, C.byref(n)), "ttn_workspace_size")
+        return int(n.value)
+
+    def bind(self, device: int = 0, stream=None) -> None:
+        """Allocate the workspace with PyTorch on ``device`` and bind it (ttn_set_stream + ttn_set_workspace)."""
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("TTN needs a CUDA device: the library has no CPU path")
+        dev = torch.device("cuda", device)
+        n = self.ttn_workspace_size()
+        self._ws = torch.empty(n + 256, dtype=torch.uint8, device=dev)
+        base = self._ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._stream = s
+        self._check(self.lib.ttn_set_stream(self.h, C.c_void_p(s.cuda_stream)), "ttn_set_stream")
+        self._check(self.lib.ttn_set_workspace(self.h, C.c_void_p(aligned), n), "ttn_set_workspace")
+
+    def ttn_set_rdo0(self, rho0: np.ndarray) -> None:
+        r = np.ascontiguousarray(np.asarray(rho0, np.complex128)).view(np.float64)
+        self._check(self.lib.ttn_set_rdo0(self.h, ptr(r, C.c_double)), "ttn_set_rdo0")
+
+    def ttn_step(self, dt: float, scheme: int = TTN_PS1, n_steps: int = 1) -> None:
+        self._check(self.lib.ttn_step(self.h, float(dt), int(scheme), int(n_steps)), "ttn_step")
+
+    def ttn_rdm(self) -> np.ndarray:
+        out = np.zeros((self.M, self.M), np.complex128)
+        self._check(self.lib.ttn_rdm(self.h, ptr(out.view(np.float64), C.c_double)), "ttn_rdm")
+        return out
+
+    def ttn_rdm_device(self, dev_ptr: int) -> None:
+        self._check(self.lib.ttn_rdm_device(self.h, C.c_void_p(dev_ptr)), "ttn_rdm_device")
+
+    def ttn_get_ranks(self) -> np.ndarray:
+        r = np.zeros(self.n_nodes, np.int32)
+        self._check(self.lib.ttn_get_ranks(self.h, ptr(r, C.c_int32)), "ttn_get_ranks")
+        return r
+
+    def ttn_node_shape(self, u: int):
+        d = np.zeros(3, np.int32)
+        self._check(self.lib.ttn_node_shape(self.h, u, ptr(d, C.c_int32)), "ttn_node_shape")
+        return tuple(int(x) for x in d)
+
+    def ttn_get_node(self, u: int) -> np.ndarray:
+        out = np.zeros(self.ttn_node_shape(u), np.complex128)
+        self._check(self.lib.ttn_get_node(self.h, u, ptr(out.view(np.float64), C.c_double)), "ttn_get_node")
+        return out
+
+    def ttn_set_node(self, u: int, T: np.ndarray) -> None:
+        a = np.ascontiguousarray(np.asarray(T, np.complex128))
+        if a.shape != self.ttn_node_shape(u):
+            raise ValueError("node tensor shape mismatch")
+        self._check(self.lib.ttn_set_node(self.h, u, ptr(a.view(np.float64), C.c_double)), "ttn_set_node")
+
+    def ttn_time(self) -> float:
+        t = C.c_double()
+        self._check(self.lib.ttn_time(self.h, C.byref(t)), "ttn_time")
+        return t.value
+
+    def ttn_stats(self, kind: int):
+        n, f = C.c_int64(), C.c_double()
+        self._check(self.lib.ttn_stats(self.h, kind, C.byref(n), C.byref(f)), "ttn_stats")
+        return int(n.value), float(f.value)
+
+    def ttn_profile(self, on: bool) -> None:
+        self._check(self.lib.ttn_profile(self.h, 1 if on else 0), "ttn_profile")
+
+    def ttn_profile_read(self, kind: int) -> float:
+        ms = C.c_double()
+        self._check(self.lib.ttn_profile_read(self.h, kind, C.byref(ms)), "ttn_profile_read")
+        return float(ms.value)
+
+    def ttn_stats_reset(self) -> None:
+        self._check(self.lib.ttn_stats_reset(self.h), "ttn_stats_reset")
+
+    def ttn_substeps(self, tau: float) -> int:
+        m = C.c_int32()
+        self._check(self.lib.ttn_substeps(self.h, float(tau), C.byref(m)), "ttn_substeps")
+        return int(m.value)
+
+
+def from_model(H, baths, depth, parent, leg_node, ranks, rho0=None, drives=(), precision=TTN_FP64,
+               params: Optional[dict] = None, device: int = 0, stream=None) -> TTN:
+    """Build, load and bind a TTN for the HEOM of system ``H`` with ``baths``
+    (objects with Q, beta, dl, bo, n_ltc, scheme) and ``drives`` (objects with
+    V, g(t), bound)."""
+    M = np.asarray(H).shape[0]
+    t = TTN(parent, leg_node, [M, M] + list(depth), ranks, precision)
+    if params:
+        t.ttn_set_params(**params)
+    t.sop_load(heom.heom_sop(H, baths, depth, drives))
+    for d, dr in enumerate(drives):
+        t.ttn_set_drive(d, dr.g, dr.bound)
+    t.bind(device, stream)
+    if rho0 is not None:
+        t.ttn_set_rdo0(rho0)
+    return t

@@ -1,0 +1,741 @@
+// C ABI of the TTN-HEOM library (include/ttn_heom.h): handle, workspace layout
+// and the host-side sweep executor that issues the kernels of kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ttn_heom.h"
+#include "kernels.cuh"
+#include "plan.hpp"
+
+using namespace ttn;
+
+namespace {
+
+struct DriveSlot {
+  ttn_drive_fn fn = nullptr;
+  void* user = nullptr;
+  double bound = 1.0;
+};
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+}  // namespace
+
+struct ttn_ctx {
+  Plan plan;
+  int precision = TTN_FP64;
+  ttn_params params{1e-12, 2.5, 1e-7, 2.0, 32, 1e-12};
+  bool sop_loaded = false;
+  bool ws_bound = false;
+  bool envs_dirty = true;
+  std::vector<DriveSlot> drives;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double t = 0.0;
+
+  // workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  std::vector<double2*> h_bufs;  // device addresses per buffer id
+  std::vector<double2*> h_mats;  // device addresses per matrix id
+  double2* pool = nullptr;
+  double2* qr_work = nullptr;
+  double2* rdm_vec = nullptr;
+  double2* rho_dev = nullptr;
+  int* flag_dev = nullptr;
+  DriveMat* drive_list_dev = nullptr;
+  std::vector<DriveMat> drive_list;
+  std::vector<int64_t> rdm_off;  // per node offset into rdm_vec
+  DevTables T{};
+
+  // kernel accounting (ttn_stats / ttn_profile)
+  int64_t n_launch[4] = {0, 0, 0, 0};
+  double n_flops[4] = {0, 0, 0, 0};
+  bool profiling = false;
+  struct Mark {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<Mark> marks;
+  double prof_ms[4] = {0, 0, 0, 0};
+
+  ~ttn_ctx() {
+    for (auto& m : marks) {
+      cudaEventDestroy(m.a);
+      cudaEventDestroy(m.b);
+    }
+    for (auto e : ev_free) cudaEventDestroy(e);
+  }
+  cudaEvent_t get_event() {
+    if (!ev_free.empty()) {
+      cudaEvent_t e = ev_free.back();
+      ev_free.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // synchronise and fold recorded event pairs into prof_ms
+  cudaError_t drain_marks() {
+    if (marks.empty()) return cudaSuccess;
+    cudaError_t err = cudaEventSynchronize(marks.back().b);
+    if (err != cudaSuccess) return err;
+    for (auto& m : marks) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) prof_ms[m.kind] += ms;
+      ev_free.push_back(m.a);
+      ev_free.push_back(m.b);
+    }
+    marks.clear();
+    return cudaSuccess;
+  }
+
+  ttn_status fail(ttn_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+};
+
+namespace {
+
+ttn_status cuda_fail(ttn_t h, cudaError_t e, const char* what) {
+  return h->fail(TTN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(h, call)                                   \
+  do {                                                      \
+    cudaError_t _e = (call);                                \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, #call);  \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Workspace layout
+// ---------------------------------------------------------------------------
+struct Layout {
+  size_t nodes, pool, scratch, qr, rdm, rho, bufs_tab, mats_tab, terms, outs, pjs, drives, flag, total;
+  std::vector<int64_t> node_off;  // complex elements from `nodes`
+  std::vector<int64_t> rdm_off;
+  int64_t scratch_elems = 0, qr_elems = 0, rdm_elems = 0;
+};
+
+Layout layout_of(const Plan& p) {
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align_up(std::max<size_t>(bytes, 1));
+    return o;
+  };
+  const int n = p.tree.n_nodes;
+  L.node_off.resize(n);
+  int64_t acc = 0;
+  for (int u = 0; u < n; ++u) {
+    L.node_off[u] = acc;
+    acc += (p.P[u] + 15) / 16 * 16;
+  }
+  L.nodes = take(acc * sizeof(double2));
+  L.pool = take(std::max<int64_t>(p.mat_pool, 1) * sizeof(double2));
+  const int64_t r2 = (int64_t)p.r_max * p.r_max;
+  const int64_t nP = (int64_t)(3 + p.buf.n_t + p.buf.n_w) * p.P_max;
+  L.scratch_elems = nP + 3 * r2;
+  L.scratch = take(L.scratch_elems * sizeof(double2));
+  L.qr_elems = p.P_max;
+  L.qr = take(L.qr_elems * sizeof(double2));
+  L.rdm_off.resize(n);
+  int64_t ra = 0;
+  for (int u = 0; u < n; ++u) {
+    L.rdm_off[u] = ra;
+    ra += p.dims[u][0];
+  }
+  L.rdm_elems = ra;
+  L.rdm = take(ra * sizeof(double2));
+  L.rho = take((size_t)p.leg_dims[0] * p.leg_dims[0] * sizeof(double2));
+  L.bufs_tab = take(p.buf.n_bufs * sizeof(double2*));
+  L.mats_tab = take(p.mats.size() * sizeof(double2*));
+  L.terms = take(p.ap_terms.size() * sizeof(ApTerm));
+  L.outs = take(p.ap_outs.size() * sizeof(ApOut));
+  L.pjs = take(p.pj_outs.size() * sizeof(PjOut));
+  L.drives = take(p.locals.size() * sizeof(DriveMat));
+  L.flag = take(sizeof(int) * 4);
+  L.total = off;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// Executor: the ps1 sweep of the oracle, issued as kernels on h->stream
+// ---------------------------------------------------------------------------
+struct Exec {
+  ttn_t h;
+  Plan& p;
+  cudaStream_t s;
+  explicit Exec(ttn_t hh) : h(hh), p(hh->plan), s(hh->stream) {}
+
+  // account one kernel launch of class `kind` and, when profiling, bracket it
+  // with CUDA events on the handle's stream
+  template <typename F>
+  void run(int kind, double flops, F&& launch) {
+    h->n_launch[kind] += 1;
+    h->n_flops[kind] += flops;
+    if (!h->profiling) {
+      launch();
+      return;
+    }
+    cudaEvent_t a = h->get_event(), b = h->get_event();
+    cudaEventRecord(a, s);
+    launch();
+    cudaEventRecord(b, s);
+    h->marks.push_back({kind, a, b});
+    if (h->marks.size() > 100000) h->drain_marks();
+  }
+  void apply(int kind, int list, const Epi& e) {
+    if (list < 0) return;
+    const ApList& L = p.ap_lists[list];
+    run(kind, L.flops, [&] { launch_apply(h->T, L, e, s); });
+  }
+  void store(int kind, int list) { apply(kind, list, Epi{EPI_STORE, 0, 0, 0, 0.0}); }
+
+  void env(int a, int b) {
+    const EnvLists& E = p.env[p.dir_id(a, b)];
+    store(1, E.first);
+    store(1, E.classes);
+    if (E.project >= 0) {
+      const PjList& L = p.pj_lists[E.project];
+      run(1, L.flops, [&] { launch_project(h->T, L, s); });
+    }
+  }
+  // U_u := Q (semi-unitary toward neighbour v), R -> bond buffer
+  void qr(int u, int v) {
+    const int li = p.tree.leg_index(u, v);
+    const auto& d = p.dims[u];
+    const double n = d[li], m = (double)p.P[u] / n;
+    // Householder factorisation + explicit Q: 2 (2 m n^2 - 2 n^3 / 3) complex MACs
+    const double flops = 8.0 * 2.0 * (2.0 * m * n * n - 2.0 * n * n * n / 3.0);
+    run(2, flops, [&] {
+      launch_qr(h->h_bufs[u], d[0], d[1], d[2], li, h->params.qr_tol, h->qr_work,
+                h->h_bufs[p.buf.tmp], h->h_bufs[p.buf.bond_y], h->flag_dev, s);
+    });
+  }
+  // U_v := R x_(leg of v facing u) U_v
+  void absorb(int v, int u) {
+    const int li = p.tree.leg_index(v, u);
+    store(3, p.absorb[v][li]);
+    run(3, 0.0, [&] { launch_copy(h->h_bufs[v], h->h_bufs[p.buf.tmp], p.P[v], s); });
+  }
+  void rk4(const FlowLists& F, int y, int ys, int acc, double tau) {
+    const int m = p.n_sub(tau, h->params.kappa);
+    const double hs = tau / m;
+    for (int sub = 0; sub < m; ++sub)
+      for (int st = 1; st <= 4; ++st) {
+        const int var = st == 1 ? 0 : 1;
+        store(0, F.first[var]);
+        apply(0, F.combine[var], Epi{st, y, ys, acc, hs});
+      }
+  }
+  void node_flow(int u, double tau) { rk4(p.node_flow[u], u, p.buf.ys, p.buf.acc, tau); }
+  void bond_flow(int a, int b, double tau) {
+    rk4(p.bond_flow[p.dir_id(a, b)], p.buf.bond_y, p.buf.bond_ys, p.buf.bond_acc, tau);
+  }
+
+  // Lie-Trotter half sweep Phi_h(u) and its adjoint (see oracle/ttn.py)
+  void phi(int u, double hh, bool flow_u) {
+    for (int c : p.tree.children[u]) {
+      qr(u, c);
+      absorb(c, u);
+      env(u, c);
+      phi(c, hh, true);
+      qr(c, u);
+      env(c, u);
+      bond_flow(c, u, -hh);
+      absorb(u, c);
+    }
+    if (flow_u) node_flow(u, hh);
+  }
+  void phi_adj(int u, double hh, bool flow_u) {
+    if (flow_u) node_flow(u, hh);
+    const auto& ch = p.tree.children[u];
+    for (auto it = ch.rbegin(); it != ch.rend(); ++it) {
+      const int c = *it;
+      qr(u, c);
+      env(u, c);
+      bond_flow(u, c, -hh);
+      absorb(c, u);
+      phi_adj(c, hh, true);
+      qr(c, u);
+      env(c, u);
+      absorb(u, c);
+    }
+  }
+  void drive(double t) {
+    if (h->drive_list.empty()) return;
+    DriveArgs g{};
+    for (size_t d = 0; d < h->drives.size() && d < (size_t)kMaxDrives; ++d)
+      g.g[d] = h->drives[d].fn ? h->drives[d].fn(t, h->drives[d].user) : 0.0;
+    run(3, 0.0, [&] { launch_drive(h->T.mats, h->drive_list_dev, (int)h->drive_list.size(), g, s); });
+  }
+  void step_ps1(double dt, double t0) {
+    const double hh = 0.5 * dt;
+    if (p.n_drives == 0) {
+      phi(0, hh, false);
+      node_flow(0, dt);
+      phi_adj(0, hh, false);
+    } else {
+      drive(t0 + 0.25 * dt);
+      phi(0, hh, true);
+      drive(t0 + 0.75 * dt);
+      phi_adj(0, hh, true);
+    }
+  }
+  void rebuild_envs() {
+    drive(h->t);
+    for (int c : p.tree.postorder)
+      if (c != 0) env(c, p.tree.parent[c]);
+  }
+  void rdm(double2* out) {
+    for (int u : p.tree.postorder) {
+      const auto& d = p.dims[u];
+      const double2* w[3] = {nullptr, nullptr, nullptr};
+      for (int li = (u == 0 ? 2 : 1); li < 3; ++li) {
+        const Leg& L = p.tree.legs[u][li];
+        if (L.kind == 'n') w[li] = h->rdm_vec + h->rdm_off[L.v];
+      }
+      run(3, 0.0, [&] {
+        launch_rdm_node(h->h_bufs[u], d[0], d[1], d[2], u == 0, w[1], w[2],
+                        u == 0 ? out : h->rdm_vec + h->rdm_off[u], s);
+      });
+    }
+  }
+};
+
+template <typename F>
+ttn_status guarded(ttn_t h, F&& f) {
+  if (!h) return TTN_EINVAL;
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return h->fail(TTN_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return h->fail(TTN_EINVAL, e.what());
+  }
+}
+
+ttn_status status_of(const std::string& e) {
+  if (e.rfind("UNSUPPORTED", 0) == 0) return TTN_EUNSUPPORTED;
+  return TTN_EINVAL;
+}
+
+ttn_status upload_initial(ttn_t h, const double* rho0) {
+  Plan& p = h->plan;
+  const int M = p.leg_dims[0];
+  cudaStream_t s = h->stream;
+  for (int u = 0; u < p.tree.n_nodes; ++u) {
+    std::vector<double2> T((size_t)p.P[u], make_double2(0.0, 0.0));
+    const auto& d = p.dims[u];
+    if (u == 0) {
+      // legs 0, 1 (i, j) come first in the root's canonical order
+      for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j)
+          T[((size_t)i * d[1] + j) * d[2]] = make_double2(rho0[2 * (i * M + j)], rho0[2 * (i * M + j) + 1]);
+    } else {
+      const int64_t cols = (int64_t)d[1] * d[2];
+      for (int a = 0; a < d[0]; ++a) T[(size_t)a * cols + a] = make_double2(1.0, 0.0);
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_bufs[u], T.data(), T.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+  }
+  h->envs_dirty = true;
+  h->t = 0.0;
+  return TTN_OK;
+}
+
+ttn_status ensure_envs(ttn_t h) {
+  if (!h->envs_dirty) return TTN_OK;
+  Exec ex(h);
+  ex.rebuild_envs();
+  CUDA_TRY(h, cudaGetLastError());
+  h->envs_dirty = false;
+  return TTN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ttn_status ttn_create(const ttn_tree* tree, const int32_t* leg_dims, const int32_t* ranks,
+                      int32_t precision, ttn_t* out) {
+  if (!out) return TTN_EINVAL;
+  *out = nullptr;
+  if (!tree || !leg_dims || !ranks) return TTN_EINVAL;
+  if (precision != TTN_FP64 && precision != TTN_MIXED_FP32) return TTN_EINVAL;
+  ttn_t h = new (std::nothrow) ttn_ctx();
+  if (!h) return TTN_ENOMEM;
+  std::string e;
+  try {
+    e = h->plan.build(tree->n_nodes, tree->parent, tree->n_legs, tree->leg_node, leg_dims, ranks);
+  } catch (...) {
+    e = "tree construction failed";
+  }
+  if (!e.empty()) {
+    ttn_status st = status_of(e);
+    delete h;
+    return st;
+  }
+  if (precision != TTN_FP64) {
+    delete h;
+    return TTN_EUNSUPPORTED;
+  }
+  h->precision = precision;
+  *out = h;
+  return TTN_OK;
+}
+
+ttn_status ttn_set_params(ttn_t h, const ttn_params* prm) {
+  return guarded(h, [&]() -> ttn_status {
+    if (!prm) return h->fail(TTN_EINVAL, "null params");
+    if (!(prm->qr_tol >= 0) || !(prm->kappa > 0) || !(prm->ps2_atol >= 0) || !(prm->ps2_ratio >= 1) ||
+        prm->max_rank < 1 || !(prm->svd_tol >= 0))
+      return h->fail(TTN_EINVAL, "parameter out of range");
+    if (h->ws_bound && prm->max_rank != h->params.max_rank)
+      return h->fail(TTN_ESTATE, "max_rank must be set before the workspace is bound");
+    h->params = *prm;
+    return TTN_OK;
+  });
+}
+
+ttn_status ttn_get_params(ttn_t h, ttn_params* prm) {
+  if (!h || !prm) return TTN_EINVAL;
+  *prm = h->params;
+  return TTN_OK;
+}
+
+ttn_status sop_load(ttn_t h, int32_t n_ops, const int32_t* op_leg, const int64_t* op_offset,
+                    const double* op_data, int32_t n_terms, const int32_t* term_offsets,
+                    const int32_t* term_ops, const double* coef, const int32_t* coef_drive) {
+  return guarded(h, [&]() -> ttn_status {
+    if (h->ws_bound) return h->fail(TTN_ESTATE, "sop_load after the workspace was bound");
+    std::string e = h->plan.load_sop(n_ops, op_leg, op_offset, op_data, n_terms, term_offsets, term_ops,
+                                     coef, coef_drive);
+    if (!e.empty()) {
+      h->sop_loaded = false;
+      return h->fail(status_of(e), e);
+    }
+    if (h->plan.n_drives > kMaxDrives) return h->fail(TTN_EUNSUPPORTED, "at most 8 drives");
+    if ((int)h->drives.size() < h->plan.n_drives) h->drives.resize(h->plan.n_drives);
+    for (int d = 0; d < h->plan.n_drives; ++d) h->plan.drive_bound[d] = h->drives[d].bound;
+    h->plan.compute_lambda();
+    e = h->plan.build_jobs();
+    if (!e.empty()) return h->fail(TTN_EINVAL, e);
+    h->sop_loaded = true;
+    return TTN_OK;
+  });
+}
+
+ttn_status ttn_set_drive(ttn_t h, int32_t id, ttn_drive_fn g, void* user, double g_bound) {
+  return guarded(h, [&]() -> ttn_status {
+    if (id < 0 || id >= kMaxDrives) return h->fail(TTN_EINVAL, "drive id out of range");
+    if (!g || !(g_bound >= 0) || !std::isfinite(g_bound)) return h->fail(TTN_EINVAL, "bad drive");
+    if (h->ws_bound) return h->fail(TTN_ESTATE, "ttn_set_drive after the workspace was bound");
+    if ((int)h->drives.size() <= id) h->drives.resize(id + 1);
+    h->drives[id] = DriveSlot{g, user, g_bound};
+    if ((int)h->plan.drive_bound.size() <= id) h->plan.drive_bound.resize(id + 1, 1.0);
+    h->plan.drive_bound[id] = g_bound;
+    if (h->sop_loaded) h->plan.compute_lambda();
+    return TTN_OK;
+  });
+}
+
+ttn_status ttn_workspace_size(ttn_t h, size_t* bytes) {
+  return guarded(h, [&]() -> ttn_status {
+    if (!bytes) return h->fail(TTN_EINVAL, "null bytes");
+    if (!h->sop_loaded) return h->fail(TTN_ESTATE, "sop_load first");
+    *bytes = layout_of(h->plan).total;
+    return TTN_OK;
+  });
+}
+
+ttn_status ttn_set_stream(ttn_t h, void* stream) {
+  if (!h) return TTN_EINVAL;
+  h->stream = (cudaStream_t)stream;
+  return TTN_OK;
+}
+
+ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
+  return guarded(h, [&]() -> ttn_status {
+    if (!h->sop_loaded) return h->fail(TTN_ESTATE, "sop_load first");
+    if (!dptr || ((uintptr_t)dptr % kAlign) != 0) return h->fail(TTN_EINVAL, "workspace must be 256-byte aligned");
+    for (int d = 0; d < h->plan.n_drives; ++d)
+      if (!h->drives[d].fn) return h->fail(TTN_ESTATE, "a drive used by the SOP has no function");
+    Plan& p = h->plan;
+    Layout L = layout_of(p);
+    if (bytes < L.total) return h->fail(TTN_ENOMEM, "workspace smaller than ttn_workspace_size");
+    char* base = (char*)dptr;
+    h->ws = base;
+    h->ws_bytes = bytes;
+    // buffer table
+    h->h_bufs.assign(p.buf.n_bufs, nullptr);
+    double2* nodes = (double2*)(base + L.nodes);
+    for (int u = 0; u < p.tree.n_nodes; ++u) h->h_bufs[u] = nodes + L.node_off[u];
+    double2* scr = (double2*)(base + L.scratch);
+    int64_t o = 0;
+    auto nxt = [&](int64_t n) {
+      double2* q = scr + o;
+      o += n;
+      return q;
+    };
+    h->h_bufs[p.buf.ys] = nxt(p.P_max);
+    h->h_bufs[p.buf.acc] = nxt(p.P_max);
+    h->h_bufs[p.buf.tmp] = nxt(p.P_max);
+    for (int i = 0; i < p.buf.n_t; ++i) h->h_bufs[p.buf.t0 + i] = nxt(p.P_max);
+    for (int i = 0; i < p.buf.n_w; ++i) h->h_bufs[p.buf.w0 + i] = nxt(p.P_max);
+    const int64_t r2 = (int64_t)p.r_max * p.r_max;
+    h->h_bufs[p.buf.bond_y] = nxt(r2);
+    h->h_bufs[p.buf.bond_ys] = nxt(r2);
+    h->h_bufs[p.buf.bond_acc] = nxt(r2);
+    h->pool = (double2*)(base + L.pool);
+    h->h_mats.assign(p.mats.size(), nullptr);
+    for (size_t i = 0; i < p.mats.size(); ++i)
+      h->h_mats[i] = p.mats[i].off >= 0 ? h->pool + p.mats[i].off : nullptr;
+    h->h_mats[p.bond_mat] = h->h_bufs[p.buf.bond_y];
+    h->qr_work = (double2*)(base + L.qr);
+    h->rdm_vec = (double2*)(base + L.rdm);
+    h->rdm_off = L.rdm_off;
+    h->rho_dev = (double2*)(base + L.rho);
+    h->flag_dev = (int*)(base + L.flag);
+    h->T.bufs = (double2* const*)(base + L.bufs_tab);
+    h->T.mats = (double2* const*)(base + L.mats_tab);
+    h->T.terms = (const ApTerm*)(base + L.terms);
+    h->T.outs = (const ApOut*)(base + L.outs);
+    h->T.pjs = (const PjOut*)(base + L.pjs);
+    h->drive_list_dev = (DriveMat*)(base + L.drives);
+    cudaStream_t s = h->stream;
+    CUDA_TRY(h, cudaMemcpyAsync((void*)h->T.bufs, h->h_bufs.data(), h->h_bufs.size() * sizeof(double2*),
+                                cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync((void*)h->T.mats, h->h_mats.data(), h->h_mats.size() * sizeof(double2*),
+                                cudaMemcpyHostToDevice, s));
+    if (!p.ap_terms.empty())
+      CUDA_TRY(h, cudaMemcpyAsync((void*)h->T.terms, p.ap_terms.data(), p.ap_terms.size() * sizeof(ApTerm),
+                                  cudaMemcpyHostToDevice, s));
+    if (!p.ap_outs.empty())
+      CUDA_TRY(h, cudaMemcpyAsync((void*)h->T.outs, p.ap_outs.data(), p.ap_outs.size() * sizeof(ApOut),
+                                  cudaMemcpyHostToDevice, s));
+    if (!p.pj_outs.empty())
+      CUDA_TRY(h, cudaMemcpyAsync((void*)h->T.pjs, p.pj_outs.data(), p.pj_outs.size() * sizeof(PjOut),
+                                  cudaMemcpyHostToDevice, s));
+    // open-leg matrices: current = static part at g = 0; drive parts
+    h->drive_list.clear();
+    std::vector<double2> tmp;
+    auto put = [&](int slot, const std::vector<cd>& m) -> cudaError_t {
+      tmp.resize(m.size());
+      for (size_t i = 0; i < m.size(); ++i) tmp[i] = make_double2(m[i].real(), m[i].imag());
+      cudaError_t e = cudaMemcpyAsync(h->h_mats[slot], tmp.data(), tmp.size() * sizeof(double2),
+                                      cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      return e;
+    };
+    for (const LocalMat& lm : p.locals) {
+      CUDA_TRY(h, put(lm.slot, lm.stat));
+      if (lm.time_dependent) {
+        CUDA_TRY(h, put(lm.slot_stat, lm.stat));
+        DriveMat dm{};
+        dm.d = p.leg_dims[lm.leg];
+        dm.cur = lm.slot;
+        dm.stat = lm.slot_stat;
+        for (int d = 0; d < kMaxDrives; ++d) dm.part[d] = -1;
+        for (int d = 0; d < p.n_drives; ++d)
+          if (lm.slot_drive[d] >= 0) {
+            CUDA_TRY(h, put(lm.slot_drive[d], lm.drive[d]));
+            dm.part[d] = lm.slot_drive[d];
+          }
+        h->drive_list.push_back(dm);
+      }
+    }
+    if (!h->drive_list.empty())
+      CUDA_TRY(h, cudaMemcpyAsync(h->drive_list_dev, h->drive_list.data(), h->drive_list.size() * sizeof(DriveMat),
+                                  cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    h->ws_bound = true;
+    const int M = p.leg_dims[0];
+    std::vector<double> rho0(2 * M * M, 0.0);
+    rho0[0] = 1.0;
+    ttn_status st = upload_initial(h, rho0.data());
+    if (st != TTN_OK) return st;
+    return ensure_envs(h);
+  });
+}
+
+ttn_status ttn_set_rdo0(ttn_t h, const double* rho0) {
+  return guarded(h, [&]() -> ttn_status {
+    if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
+    if (!rho0) return h->fail(TTN_EINVAL, "null rho0");
+    const int M = h->plan.leg_dims[0];
+    for (int i = 0; i < 2 * M * M; ++i)
+      if (!std::isfinite(rho0[i])) return h->fail(TTN_EINVAL, "non-finite rho0");
+    ttn_status st = upload_initial(h, rho0);
+    if (st != TTN_OK) return st;
+    CUDA_TRY(h, cudaMemsetAsync(h->flag_dev, 0, sizeof(int), h->stream));
+    return ensure_envs(h);
+  });
+}
+
+ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
+  return guarded(h, [&]() -> ttn_status {
+    if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
+    if (!(std::isfinite(dt)) || dt <= 0 || n_steps < 0) return h->fail(TTN_EINVAL, "bad dt or n_steps");
+    if (scheme == TTN_VMF) return h->fail(TTN_EUNSUPPORTED, "vmf is not implemented");
+    if (scheme != TTN_PS1) {
+      if (scheme == TTN_PS2) return h->fail(TTN_EUNSUPPORTED, "ps2 is not implemented on the GPU yet");
+      return h->fail(TTN_EINVAL, "unknown scheme");
+    }
+    if (h->plan.n_sub(dt, h->params.kappa) > (1 << 20))
+      return h->fail(TTN_EINVAL, "dt * Lambda needs more than 2^20 RK4 substeps");
+    ttn_status st = ensure_envs(h);
+    if (st != TTN_OK) return st;
+    Exec ex(h);
+    for (int k = 0; k < n_steps; ++k) {
+      ex.step_ps1(dt, h->t);
+      h->t += dt;
+    }
+    ex.run(3, 0.0, [&] { launch_check_finite(h->h_bufs[0], h->plan.P[0], h->flag_dev, h->stream); });
+    CUDA_TRY(h, cudaGetLastError());
+    return TTN_OK;
+  });
+}
+
+static ttn_status check_flag(ttn_t h) {
+  int flag = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (flag) return h->fail(TTN_ENUMERIC, "non-finite amplitude in the root tensor");
+  return TTN_OK;
+}
+
+ttn_status ttn_rdm_device(ttn_t h, void* rho_dev) {
+  return guarded(h, [&]() -> ttn_status {
+    if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
+    if (!rho_dev) return h->fail(TTN_EINVAL, "null output");
+    Exec ex(h);
+    ex.rdm((double2*)rho_dev);
+    CUDA_TRY(h, cudaGetLastError());
+    return TTN_OK;
+  });
+}
+
+ttn_status ttn_rdm(ttn_t h, double* rho_out) {
+  return guarded(h, [&]() -> ttn_status {
+    if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
+    if (!rho_out) return h->fail(TTN_EINVAL, "null output");
+    Exec ex(h);
+    ex.rdm(h->rho_dev);
+    const int M = h->plan.leg_dims[0];
+    CUDA_TRY(h, cudaGetLastError());
+    CUDA_TRY(h, cudaMemcpyAsync(rho_out, h->rho_dev, (size_t)M * M * sizeof(double2), cudaMemcpyDeviceToHost,
+                                h->stream));
+    return check_flag(h);
+  });
+}
+
+ttn_status ttn_get_ranks(ttn_t h, int32_t* ranks_out) {
+  if (!h || !ranks_out) return TTN_EINVAL;
+  for (int u = 0; u < h->plan.tree.n_nodes; ++u) ranks_out[u] = u == 0 ? 0 : h->plan.ranks[u];
+  return TTN_OK;
+}
+
+ttn_status ttn_node_shape(ttn_t h, int32_t u, int32_t* dims3) {
+  if (!h || !dims3) return TTN_EINVAL;
+  if (u < 0 || u >= h->plan.tree.n_nodes) return h->fail(TTN_EINVAL, "node out of range");
+  for (int i = 0; i < 3; ++i) dims3[i] = h->plan.dims[u][i];
+  return TTN_OK;
+}
+
+ttn_status ttn_get_node(ttn_t h, int32_t u, double* host_out) {
+  return guarded(h, [&]() -> ttn_status {
+    if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
+    if (u < 0 || u >= h->plan.tree.n_nodes || !host_out) return h->fail(TTN_EINVAL, "bad node or output");
+    CUDA_TRY(h, cudaMemcpyAsync(host_out, h->h_bufs[u], h->plan.P[u] * sizeof(double2), cudaMemcpyDeviceToHost,
+                                h->stream));
+    return check_flag(h);
+  });
+}
+
+ttn_status ttn_set_node(ttn_t h, int32_t u, const double* host_in) {
+  return guarded(h, [&]() -> ttn_status {
+    if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
+    if (u < 0 || u >= h->plan.tree.n_nodes || !host_in) return h->fail(TTN_EINVAL, "bad node or input");
+    for (int64_t i = 0; i < 2 * h->plan.P[u]; ++i)
+      if (!std::isfinite(host_in[i])) return h->fail(TTN_EINVAL, "non-finite node entry");
+    CUDA_TRY(h, cudaMemcpyAsync(h->h_bufs[u], host_in, h->plan.P[u] * sizeof(double2), cudaMemcpyHostToDevice,
+                                h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->envs_dirty = true;
+    return TTN_OK;
+  });
+}
+
+ttn_status ttn_time(ttn_t h, double* t) {
+  if (!h || !t) return TTN_EINVAL;
+  *t = h->t;
+  return TTN_OK;
+}
+
+ttn_status ttn_substeps(ttn_t h, double tau, int32_t* m) {
+  if (!h || !m) return TTN_EINVAL;
+  if (!h->sop_loaded) return h->fail(TTN_ESTATE, "sop_load first");
+  *m = h->plan.n_sub(tau, h->params.kappa);
+  return TTN_OK;
+}
+
+ttn_status ttn_batch_step(ttn_t* hs, int32_t n, double dt, int32_t scheme, int32_t n_steps) {
+  if (!hs || n < 0) return TTN_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    ttn_status s = ttn_step(hs[i], dt, scheme, n_steps);
+    if (s != TTN_OK) return s;
+  }
+  return TTN_OK;
+}
+
+ttn_status ttn_stats(ttn_t h, int32_t kind, int64_t* launches, double* flops) {
+  if (!h || kind < 0 || kind > 3) return TTN_EINVAL;
+  if (launches) *launches = h->n_launch[kind];
+  if (flops) *flops = h->n_flops[kind];
+  return TTN_OK;
+}
+
+ttn_status ttn_profile(ttn_t h, int32_t on) {
+  if (!h) return TTN_EINVAL;
+  h->profiling = on != 0;
+  return TTN_OK;
+}
+
+ttn_status ttn_profile_read(ttn_t h, int32_t kind, double* ms) {
+  if (!h || kind < 0 || kind > 3 || !ms) return TTN_EINVAL;
+  CUDA_TRY(h, h->drain_marks());
+  *ms = h->prof_ms[kind];
+  return TTN_OK;
+}
+
+ttn_status ttn_stats_reset(ttn_t h) {
+  if (!h) return TTN_EINVAL;
+  CUDA_TRY(h, h->drain_marks());
+  for (int k = 0; k < 4; ++k) {
+    h->n_launch[k] = 0;
+    h->n_flops[k] = 0;
+    h->prof_ms[k] = 0;
+  }
+  return TTN_OK;
+}
+
+const char* ttn_last_error(ttn_t h) { return h ? h->err.c_str() : "null handle"; }
+
+void ttn_destroy(ttn_t h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,370 @@
+// Device kernels of the TTN-HEOM library, FP64 path (sm_103a).
+//
+// On GB300 the FP64 pipe issues about 2 FMA per SM per clock, so every kernel
+// here is bound by FP64 issue, not by memory: the data (node tensors of at most
+// a few hundred KB, environments of r x r) stays in L2 and L1.
+#include "kernels.cuh"
+
+namespace ttn {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a*b + c
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 cfma_conj(double2 a, double2 b, double2 c) {  // conj(a)*b + c
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(-a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+
+// ---------------------------------------------------------------------------
+// Sum of mode products: out_o[idx] = sum_t M_t x_{leg_t} src_t, one thread per
+// output element; the K loop runs along the leg of each term.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kApTile) k_apply(DevTables T, ApList L, Epi ep) {
+  const int tile = blockIdx.x;
+  int o = L.out_begin;
+  while (o + 1 < L.out_end && T.outs[o + 1].tile0 <= tile) ++o;
+  const ApOut out = T.outs[o];
+  const int d0 = out.d0, d1 = out.d1, d2 = out.d2;
+  const int64_t P = (int64_t)d0 * d1 * d2;
+  const int64_t idx = (int64_t)(tile - out.tile0) * kApTile + threadIdx.x;
+  if (idx >= P) return;
+  const int i2 = (int)(idx % d2);
+  const int i1 = (int)((idx / d2) % d1);
+  const int i0 = (int)(idx / ((int64_t)d1 * d2));
+  double2 acc = make_double2(0.0, 0.0);
+  for (int t = out.term_begin; t < out.term_end; ++t) {
+    const ApTerm term = T.terms[t];
+    const double2* __restrict__ src = T.bufs[term.src];
+    if (term.mat < 0) {
+      acc = cadd(acc, src[idx]);
+      continue;
+    }
+    const double2* __restrict__ M = T.mats[term.mat];
+    int dl, il;
+    int64_t stride;
+    if (term.leg == 0) {
+      dl = d0; il = i0; stride = (int64_t)d1 * d2;
+    } else if (term.leg == 1) {
+      dl = d1; il = i1; stride = d2;
+    } else {
+      dl = d2; il = i2; stride = 1;
+    }
+    const double2* __restrict__ row = M + (int64_t)il * dl;
+    const double2* __restrict__ col = src + (idx - (int64_t)il * stride);
+    for (int x = 0; x < dl; ++x) acc = cfma(row[x], col[(int64_t)x * stride], acc);
+  }
+  if (ep.mode == EPI_STORE) {
+    T.bufs[out.dst][idx] = acc;
+    return;
+  }
+  double2* __restrict__ y = T.bufs[ep.y];
+  double2* __restrict__ ys = T.bufs[ep.ys];
+  double2* __restrict__ ac = T.bufs[ep.acc];
+  const double h = ep.h;
+  switch (ep.mode) {
+    case EPI_RK1:
+      ac[idx] = acc;
+      ys[idx] = cadd(y[idx], cscale(0.5 * h, acc));
+      break;
+    case EPI_RK2:
+      ac[idx] = cadd(ac[idx], cscale(2.0, acc));
+      ys[idx] = cadd(y[idx], cscale(0.5 * h, acc));
+      break;
+    case EPI_RK3:
+      ac[idx] = cadd(ac[idx], cscale(2.0, acc));
+      ys[idx] = cadd(y[idx], cscale(h, acc));
+      break;
+    default:
+      y[idx] = cadd(y[idx], cscale(h / 6.0, cadd(ac[idx], acc)));
+      break;
+  }
+}
+
+void launch_apply(const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s) {
+  if (L.n_tiles <= 0) return;
+  k_apply<<<L.n_tiles, kApTile, 0, s>>>(T, L, e);
+}
+
+// ---------------------------------------------------------------------------
+// Environment projection E[x', x] = sum_r conj(U[.. x' ..]) W[.. x ..] over all
+// legs except `leg`; one thread per output entry.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kPjTile) k_project(DevTables T, PjList L) {
+  const int tile = blockIdx.x;
+  int o = L.out_begin;
+  while (o + 1 < L.out_end && T.pjs[o + 1].tile0 <= tile) ++o;
+  const PjOut pj = T.pjs[o];
+  const int dd[3] = {pj.d0, pj.d1, pj.d2};
+  const int64_t st[3] = {(int64_t)pj.d1 * pj.d2, pj.d2, 1};
+  const int l = pj.leg;
+  const int d = dd[l];
+  const int e = (tile - pj.tile0) * kPjTile + threadIdx.x;
+  if (e >= d * d) return;
+  const int xp = e / d, x = e % d;
+  const int la = l == 0 ? 1 : 0, lb = l == 2 ? 1 : 2;  // the two other legs
+  const double2* __restrict__ U = T.bufs[pj.u_buf] + (int64_t)xp * st[l];
+  const double2* __restrict__ W = T.bufs[pj.w_buf] + (int64_t)x * st[l];
+  double2 acc = make_double2(0.0, 0.0);
+  for (int a = 0; a < dd[la]; ++a)
+    for (int b = 0; b < dd[lb]; ++b) {
+      const int64_t off = (int64_t)a * st[la] + (int64_t)b * st[lb];
+      acc = cfma_conj(U[off], W[off], acc);
+    }
+  T.mats[pj.dst_mat][e] = acc;
+}
+
+void launch_project(const DevTables& T, const PjList& L, cudaStream_t s) {
+  if (L.n_tiles <= 0) return;
+  k_project<<<L.n_tiles, kPjTile, 0, s>>>(T, L);
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR (one CTA). A (m x n, m = P / d_leg, n = d_leg) is gathered
+// column-major into `work`; rows enumerate the two other legs in order.
+// Convention (identical to the CPU oracle): for column j with remainder x of
+// norm alpha, alpha <= tol*||A||_F means no reflector (R_jj = 0, Q column
+// H_0..H_{j-1} e_j); otherwise v = x + phi*alpha*e_0 with phi = x_0/|x_0|
+// (1 if x_0 = 0), H = I - beta v v^H, beta = 2 / (v^H v) = 1/(alpha(alpha+|x_0|)).
+// Afterwards rows of R and columns of Q are rescaled so that diag(R) >= 0.
+// ---------------------------------------------------------------------------
+constexpr int kQrThreads = 512;
+constexpr int kQrMaxN = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+  v.x = warp_sum(v.x);
+  v.y = warp_sum(v.y);
+  return v;
+}
+// Block-wide sum with a fixed reduction order (deterministic).
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  return s;
+}
+
+__global__ void __launch_bounds__(kQrThreads) k_qr(double2* U, int d0, int d1, int d2, int leg,
+                                                   double tol, double2* A, double2* Q, double2* R, int* flag) {
+  __shared__ double red[kQrThreads / 32];
+  __shared__ double s_beta[kQrMaxN];
+  __shared__ int s_skip[kQrMaxN];
+  __shared__ double2 s_rdiag[kQrMaxN];
+  __shared__ double2 s_phase[kQrMaxN];
+  const int dd[3] = {d0, d1, d2};
+  const int64_t st[3] = {(int64_t)d1 * d2, d2, 1};
+  const int n = dd[leg];
+  const int la = leg == 0 ? 1 : 0, lb = leg == 2 ? 1 : 2;
+  const int64_t m = (int64_t)dd[la] * dd[lb];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  // gather A[r, c] (column-major), r = (a, b) over the two other legs
+  double fro = 0.0;
+  for (int64_t k = tid; k < m * n; k += nt) {
+    const int64_t c = k / m, r = k % m;
+    const int64_t a = r / dd[lb], b = r % dd[lb];
+    const double2 v = U[c * st[leg] + a * st[la] + b * st[lb]];
+    A[k] = v;
+    fro += v.x * v.x + v.y * v.y;
+  }
+  fro = sqrt(block_sum(fro, red));
+  if (!isfinite(fro)) {  // non-finite or overflowing input: report, leave U untouched
+    if (tid == 0) atomicOr(flag, 1);
+    return;
+  }
+  const double thr = tol * fro;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    double2* x = A + (int64_t)j * m;
+    double ss = 0.0;
+    for (int64_t r = j + tid; r < m; r += nt) ss += x[r].x * x[r].x + x[r].y * x[r].y;
+    const double alpha = sqrt(block_sum(ss, red));
+    if (alpha <= thr) {
+      for (int64_t r = j + tid; r < m; r += nt) x[r] = make_double2(0.0, 0.0);
+      if (tid == 0) {
+        s_skip[j] = 1;
+        s_beta[j] = 0.0;
+        s_rdiag[j] = make_double2(0.0, 0.0);
+        s_phase[j] = make_double2(1.0, 0.0);
+      }
+      __syncthreads();
+      continue;
+    }
+    const double2 x0 = x[j];
+    const double ax0 = hypot(x0.x, x0.y);
+    const double2 phi = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+    const double beta = 1.0 / (alpha * (alpha + ax0));
+    __syncthreads();
+    if (tid == 0) {
+      x[j] = make_double2(x0.x + phi.x * alpha, x0.y + phi.y * alpha);  // v_0
+      s_skip[j] = 0;
+      s_beta[j] = beta;
+      s_rdiag[j] = make_double2(-phi.x * alpha, -phi.y * alpha);
+      s_phase[j] = make_double2(-phi.x, -phi.y);  // R_jj / |R_jj|
+    }
+    __syncthreads();
+    // apply H_j to the remaining columns: one warp per column
+    for (int k = j + 1 + wid; k < n; k += nw) {
+      double2* a = A + (int64_t)k * m;
+      double2 w = make_double2(0.0, 0.0);
+      for (int64_t r = j + lane; r < m; r += 32) w = cfma_conj(x[r], a[r], w);
+      w = warp_sum2(w);
+      const double2 bw = cscale(beta, w);
+      for (int64_t r = j + lane; r < m; r += 32) {
+        const double2 t = cmul(x[r], bw);
+        a[r] = make_double2(a[r].x - t.x, a[r].y - t.y);
+      }
+    }
+    __syncthreads();
+  }
+  // R (row-major n x n) with diag(R) real >= 0: row j scaled by conj(phase_j)
+  for (int k = tid; k < n * n; k += nt) {
+    const int i = k / n, c = k % n;
+    double2 v = make_double2(0.0, 0.0);
+    if (c == i) {
+      v = s_skip[i] ? make_double2(0.0, 0.0) : make_double2(hypot(s_rdiag[i].x, s_rdiag[i].y), 0.0);
+    } else if (c > i) {
+      const double2 a = A[(int64_t)c * m + i];
+      const double2 p = s_phase[i];
+      v = make_double2(a.x * p.x + a.y * p.y, a.y * p.x - a.x * p.y);  // conj(p) * a
+    }
+    R[k] = v;
+  }
+  // Q = H_0 ... H_{n-1} [I; 0], column-major in Q
+  for (int64_t k = tid; k < m * n; k += nt) {
+    const int64_t c = k / m, r = k % m;
+    Q[k] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {
+    if (s_skip[j]) continue;
+    const double2* v = A + (int64_t)j * m;
+    const double beta = s_beta[j];
+    for (int k = j + wid; k < n; k += nw) {
+      double2* q = Q + (int64_t)k * m;
+      double2 w = make_double2(0.0, 0.0);
+      for (int64_t r = j + lane; r < m; r += 32) w = cfma_conj(v[r], q[r], w);
+      w = warp_sum2(w);
+      const double2 bw = cscale(beta, w);
+      for (int64_t r = j + lane; r < m; r += 32) {
+        const double2 t = cmul(v[r], bw);
+        q[r] = make_double2(q[r].x - t.x, q[r].y - t.y);
+      }
+    }
+    __syncthreads();
+  }
+  // scatter Q (columns scaled by phase) back into the node layout
+  for (int64_t k = tid; k < m * n; k += nt) {
+    const int64_t c = k / m, r = k % m;
+    const int64_t a = r / dd[lb], b = r % dd[lb];
+    U[c * st[leg] + a * st[la] + b * st[lb]] = cmul(Q[k], s_phase[c]);
+  }
+}
+
+void launch_qr(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work,
+               double2* qbuf, double2* R, int* flag, cudaStream_t s) {
+  k_qr<<<1, kQrThreads, 0, s>>>(U, d0, d1, d2, leg, tol, work, qbuf, R, flag);
+}
+
+__global__ void k_copy(double2* dst, const double2* src, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+void launch_copy(double2* dst, const double2* src, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  k_copy<<<blocks, 256, 0, s>>>(dst, src, n);
+}
+
+// ---------------------------------------------------------------------------
+// Reduced density matrix (rho_S = <0|Omega>): contraction of one node with
+// the vectors of its two child legs (the n = 0 unit vector on open legs).
+// ---------------------------------------------------------------------------
+__global__ void k_rdm_node(const double2* U, int d0, int d1, int d2, int root, const double2* w1,
+                           const double2* w2, double2* out) {
+  // root: out[i*d1 + j] = sum_c U[i, j, c] w2[c]; else out[a] = sum_{b,c} U[a,b,c] w1[b] w2[c]
+  const int nout = root ? d0 * d1 : d0;
+  for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < nout; e += blockDim.x * gridDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    if (root) {
+      const double2* row = U + (int64_t)e * d2;
+      if (w2) {
+        for (int c = 0; c < d2; ++c) acc = cfma(row[c], w2[c], acc);
+      } else {
+        acc = row[0];
+      }
+    } else {
+      const double2* blk = U + (int64_t)e * d1 * d2;
+      for (int b = 0; b < (w1 ? d1 : 1); ++b) {
+        double2 inner = make_double2(0.0, 0.0);
+        const double2* row = blk + (int64_t)b * d2;
+        if (w2) {
+          for (int c = 0; c < d2; ++c) inner = cfma(row[c], w2[c], inner);
+        } else {
+          inner = row[0];
+        }
+        acc = w1 ? cfma(w1[b], inner, acc) : inner;
+      }
+    }
+    out[e] = acc;
+  }
+}
+void launch_rdm_node(const double2* U, int d0, int d1, int d2, bool root, const double2* w1,
+                     const double2* w2, double2* out, cudaStream_t s) {
+  const int nout = root ? d0 * d1 : d0;
+  k_rdm_node<<<(nout + 127) / 128, 128, 0, s>>>(U, d0, d1, d2, root ? 1 : 0, w1, w2, out);
+}
+
+__global__ void k_drive(double2* const* mats, const DriveMat* list, int n, DriveArgs g) {
+  const DriveMat dm = list[blockIdx.x];
+  const int dd = dm.d * dm.d;
+  double2* cur = mats[dm.cur];
+  const double2* st = mats[dm.stat];
+  for (int e = threadIdx.x; e < dd; e += blockDim.x) {
+    double2 v = st[e];
+    for (int d = 0; d < kMaxDrives; ++d)
+      if (dm.part[d] >= 0) {
+        const double2 p = mats[dm.part[d]][e];
+        v.x += g.g[d] * p.x;
+        v.y += g.g[d] * p.y;
+      }
+    cur[e] = v;
+  }
+}
+void launch_drive(double2* const* mats_dev, const DriveMat* list, int n, const DriveArgs& g,
+                  cudaStream_t s) {
+  if (n <= 0) return;
+  k_drive<<<n, 128, 0, s>>>(mats_dev, list, n, g);
+}
+
+__global__ void k_check_finite(const double2* x, int64_t n, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    if (!isfinite(v.x) || !isfinite(v.y)) atomicOr(flag, 1);
+  }
+}
+void launch_check_finite(const double2* x, int64_t n, int* flag, cudaStream_t s) {
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 64);
+  k_check_finite<<<blocks, 256, 0, s>>>(x, n, flag);
+}
+
+}  // namespace ttn

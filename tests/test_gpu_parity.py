@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs. Tolerance: RDM max-abs <= 1e-6 for the FP64 path (the
+stated bar); short runs are held to 1e-10 since both sides run the same
+algorithm in FP64 and differ only by rounding order."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ttn as ottn
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL_SHORT = 1e-10
+TOL_FP64 = 1e-6
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2603_17711_gb300 as p
+    p.library()
+    return p
+
+
+def gpu_from(pkg, w, **kw):
+    return pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0,
+                          drives=w.drives, **kw)
+
+
+def run_both(pkg, w, n, scheme="ps1", oracle_setup=None, gpu_setup=None):
+    g = gpu_from(pkg, w)
+    o = ottn.from_workload(w)
+    if oracle_setup:
+        oracle_setup(o)
+    if gpu_setup:
+        gpu_setup(g)
+    assert list(g.ttn_get_ranks()) == o.ranks
+    err = float(np.max(np.abs(g.ttn_rdm() - o.rdm())))
+    code = pkg.TTN_PS1 if scheme == "ps1" else pkg.TTN_PS2
+    for _ in range(n):
+        g.ttn_step(w.dt, code, 1)
+        o.step(w.dt, scheme)
+        err = max(err, float(np.max(np.abs(g.ttn_rdm() - o.rdm()))))
+    return err, g, o
+
+
+@pytest.mark.parametrize("tree", ["tt", "btt"])
+def test_spin_boson_small(pkg, tree):
+    w = W.spin_boson_tt(depth=6, n_pade=3, rank=6, tree=tree)
+    err, g, _ = run_both(pkg, w, 15)
+    g.close()
+    assert err <= TOL_SHORT
+
+
+def test_untruncated_ranks(pkg):
+    w = W.spin_boson_tt(depth=4, n_pade=2, rank=1000)
+    err, g, _ = run_both(pkg, w, 20)
+    g.close()
+    assert err <= TOL_SHORT
+
+
+def test_multibath_exciton_chain_small(pkg):
+    w = W.exciton_chain(n_sites=3, rank=7, depth=4, n_steps=8)
+    err, g, _ = run_both(pkg, w, 8)
+    g.close()
+    assert err <= TOL_SHORT
+
+
+def test_driven_two_level_system(pkg):
+    w = W.spin_boson_tt(depth=5, n_pade=2, rank=5, tree="btt")
+    w.drives = [W.Drive(V=W.SIGMA_X, amp=0.5, omega=3.0)]
+    err, g, _ = run_both(pkg, w, 12)
+    g.close()
+    assert err <= TOL_SHORT
+
+
+def test_structured_bath_brownian_features(pkg):
+    w = W.driven_structured_tls(n_pade=2, depth=4)
+    w.scheme = "ps1"
+    w.ranks = W.uniform_ranks(w.parent, 6)
+    err, g, _ = run_both(pkg, w, 6)
+    g.close()
+    assert err <= TOL_SHORT
+
+
+@pytest.mark.parametrize("K,tree,rank", [(1, "tt", 3), (2, "tt", 1), (2, "btt", 2), (5, "btt", 1)])
+def test_edge_shapes(pkg, K, tree, rank):
+    # K = 1: a single root node with no bonds; rank 1 bonds; odd binary splits
+    w = W.spin_boson_tt(depth=3, n_pade=K - 1, rank=rank, tree=tree)
+    err, g, _ = run_both(pkg, w, 6)
+    g.close()
+    assert err <= TOL_SHORT
+
+
+def test_depth_one_legs_and_random_rho0(pkg):
+    rng = np.random.default_rng(21)
+    w = W.spin_boson_tt(depth=1, n_pade=2, rank=2)
+    w.rho0 = W.random_density_matrix(rng, 2)
+    err, g, _ = run_both(pkg, w, 5)
+    g.close()
+    assert err <= TOL_SHORT
+
+
+def test_generic_state_via_set_node(pkg):
+    # start both sides from the same generic TTN (HTD of a random EDO) to
+    # exercise every kernel away from the sparse product state
+    w = W.spin_boson_tt(depth=4, n_pade=3, rank=5, tree="btt")
+    rng = np.random.default_rng(5)
+    o = ottn.from_workload(w)
+    full = rng.normal(size=w.leg_dims) + 1j * rng.normal(size=w.leg_dims)
+    tensors = ottn.htd_tensors(o.tree, o.leg_dims, o.ranks, full)
+
+    def setup_oracle(st):
+        st.tensors = [t.copy() for t in tensors]
+        for c in st.tree.postorder():
+            if c:
+                st.update_env(c, st.tree.parent[c])
+
+    def setup_gpu(g):
+        for u, t in enumerate(tensors):
+            g.ttn_set_node(u, t)
+
+    err, g, o = run_both(pkg, w, 5, oracle_setup=setup_oracle, gpu_setup=setup_gpu)
+    for u in range(len(w.parent)):
+        assert np.max(np.abs(g.ttn_get_node(u) - o.tensors[u])) < 1e-10
+    g.close()
+    assert err <= TOL_SHORT * 10
+
+
+def test_spin_boson_tt_1000_steps_against_stored_oracle(pkg):
+    """Full spin-boson tensor-train workload (K=4, depth 10, rank 10, dt 0.01,
+    1000 steps) against the oracle trajectory stored by tests/golden/make_golden.py."""
+    rows = np.loadtxt(os.path.join(HERE, "golden", "spin_boson_tt_k4_n10_r10.txt"))
+    steps = rows[:, 0].astype(int)
+    ref = (rows[:, 1::2] + 1j * rows[:, 2::2]).reshape(-1, 2, 2)
+    w = W.spin_boson_tt(n_steps=1000)
+    g = gpu_from(pkg, w)
+    err, n = 0.0, 0
+    for k, s in enumerate(steps):
+        if s > n:
+            g.ttn_step(w.dt, pkg.TTN_PS1, int(s - n))
+            n = int(s)
+        err = max(err, float(np.max(np.abs(g.ttn_rdm() - ref[k]))))
+    g.close()
+    assert err <= TOL_FP64
+    assert err <= 1e-9  # observed far below the bar; flag drifts early
+
+
+def test_exciton_chain_full_size_first_steps(pkg):
+    """The 7-site chain at full size (21 features, depth 8, rank 20, 21 nodes):
+    the oracle is slow there, so two steps are compared element by element."""
+    w = W.exciton_chain(n_steps=2)
+    err, g, _ = run_both(pkg, w, 2)
+    g.close()
+    assert err <= TOL_SHORT
+
+
+def test_bitwise_deterministic(pkg):
+    w = W.spin_boson_tt(depth=6, n_pade=3, rank=6, tree="btt")
+    outs = []
+    for _ in range(2):
+        g = gpu_from(pkg, w)
+        g.ttn_step(w.dt, pkg.TTN_PS1, 10)
+        outs.append(g.ttn_rdm())
+        g.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_overflow_is_reported_as_numeric_error(pkg):
+    w = W.spin_boson_tt(depth=3, n_pade=1, rank=2)
+    w.rho0 = np.array([[1e308, 0], [0, 0]], complex)  # finite, but the first RK4 stage overflows
+    g = gpu_from(pkg, w)
+    g.ttn_step(w.dt, pkg.TTN_PS1, 1)
+    with pytest.raises(pkg.TTNError) as e:
+        g.ttn_rdm()
+    assert e.value.status == 4  # TTN_ENUMERIC
+    g.close()
+
+
+def test_vmf_and_ps2_status(pkg):
+    w = W.spin_boson_tt(depth=3, n_pade=1, rank=2)
+    g = gpu_from(pkg, w)
+    with pytest.raises(pkg.TTNError) as e:
+        g.ttn_step(w.dt, pkg.TTN_VMF, 1)
+    assert e.value.status == 7
+    g.close()
