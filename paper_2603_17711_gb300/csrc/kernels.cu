@@ -28,43 +28,61 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
 
 // ---------------------------------------------------------------------------
-// Sum of mode products: out_o[idx] = sum_t M_t x_{leg_t} src_t, one thread per
-// output element; the K loop runs along the leg of each term.
+// Sum of mode products: out_o[idx] = sum_t M_t x_{leg_t} src_t.
+// A CTA owns 32 consecutive output elements (one per lane); its 8 warps split
+// the term list (warp w takes terms w, w+8, ...) and the partial sums are
+// added in a fixed order in shared memory, so results are bitwise
+// reproducible. FP64 issue (~2 FMA/clk/SM) is the bound: the mapping spreads
+// a node application over as many SMs as possible.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kApTile) k_apply(DevTables T, ApList L, Epi ep) {
+constexpr int kApWarps = 8;
+
+__device__ __forceinline__ double2 term_dot(const ApTerm& term, const DevTables& T, int64_t idx, int i0, int i1,
+                                            int i2, int d0, int d1, int d2) {
+  const double2* __restrict__ src = T.bufs[term.src];
+  if (term.mat < 0) return src[idx];
+  const double2* __restrict__ M = T.mats[term.mat];
+  int dl, il;
+  int64_t stride;
+  if (term.leg == 0) {
+    dl = d0; il = i0; stride = (int64_t)d1 * d2;
+  } else if (term.leg == 1) {
+    dl = d1; il = i1; stride = d2;
+  } else {
+    dl = d2; il = i2; stride = 1;
+  }
+  const double2* __restrict__ row = M + (int64_t)il * dl;
+  const double2* __restrict__ col = src + (idx - (int64_t)il * stride);
+  double2 acc = make_double2(0.0, 0.0);
+  for (int x = 0; x < dl; ++x) acc = cfma(row[x], col[(int64_t)x * stride], acc);
+  return acc;
+}
+
+__global__ void __launch_bounds__(32 * kApWarps) k_apply(DevTables T, ApList L, Epi ep) {
+  __shared__ double2 part[kApWarps][32];
   const int tile = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int o = L.out_begin;
   while (o + 1 < L.out_end && T.outs[o + 1].tile0 <= tile) ++o;
   const ApOut out = T.outs[o];
   const int d0 = out.d0, d1 = out.d1, d2 = out.d2;
   const int64_t P = (int64_t)d0 * d1 * d2;
-  const int64_t idx = (int64_t)(tile - out.tile0) * kApTile + threadIdx.x;
-  if (idx >= P) return;
-  const int i2 = (int)(idx % d2);
-  const int i1 = (int)((idx / d2) % d1);
-  const int i0 = (int)(idx / ((int64_t)d1 * d2));
+  const int64_t idx = (int64_t)(tile - out.tile0) * kApTile + lane;
   double2 acc = make_double2(0.0, 0.0);
-  for (int t = out.term_begin; t < out.term_end; ++t) {
-    const ApTerm term = T.terms[t];
-    const double2* __restrict__ src = T.bufs[term.src];
-    if (term.mat < 0) {
-      acc = cadd(acc, src[idx]);
-      continue;
+  if (idx < P) {
+    const int i2 = (int)(idx % d2);
+    const int i1 = (int)((idx / d2) % d1);
+    const int i0 = (int)(idx / ((int64_t)d1 * d2));
+    for (int t = out.term_begin + wid; t < out.term_end; t += kApWarps) {
+      const double2 v = term_dot(T.terms[t], T, idx, i0, i1, i2, d0, d1, d2);
+      acc = cadd(acc, v);
     }
-    const double2* __restrict__ M = T.mats[term.mat];
-    int dl, il;
-    int64_t stride;
-    if (term.leg == 0) {
-      dl = d0; il = i0; stride = (int64_t)d1 * d2;
-    } else if (term.leg == 1) {
-      dl = d1; il = i1; stride = d2;
-    } else {
-      dl = d2; il = i2; stride = 1;
-    }
-    const double2* __restrict__ row = M + (int64_t)il * dl;
-    const double2* __restrict__ col = src + (idx - (int64_t)il * stride);
-    for (int x = 0; x < dl; ++x) acc = cfma(row[x], col[(int64_t)x * stride], acc);
   }
+  part[wid][lane] = acc;
+  __syncthreads();
+  if (wid != 0 || idx >= P) return;
+  acc = part[0][lane];
+  for (int w = 1; w < kApWarps; ++w) acc = cadd(acc, part[w][lane]);
   if (ep.mode == EPI_STORE) {
     T.bufs[out.dst][idx] = acc;
     return;
@@ -94,15 +112,20 @@ __global__ void __launch_bounds__(kApTile) k_apply(DevTables T, ApList L, Epi ep
 
 void launch_apply(const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s) {
   if (L.n_tiles <= 0) return;
-  k_apply<<<L.n_tiles, kApTile, 0, s>>>(T, L, e);
+  k_apply<<<L.n_tiles, 32 * kApWarps, 0, s>>>(T, L, e);
 }
 
 // ---------------------------------------------------------------------------
 // Environment projection E[x', x] = sum_r conj(U[.. x' ..]) W[.. x ..] over all
-// legs except `leg`; one thread per output entry.
+// legs except `leg`. A CTA owns 32 output entries (one per lane); its 8 warps
+// split the reduction range and are summed in a fixed order.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kPjTile) k_project(DevTables T, PjList L) {
+constexpr int kPjWarps = 8;
+
+__global__ void __launch_bounds__(32 * kPjWarps) k_project(DevTables T, PjList L) {
+  __shared__ double2 part[kPjWarps][32];
   const int tile = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int o = L.out_begin;
   while (o + 1 < L.out_end && T.pjs[o + 1].tile0 <= tile) ++o;
   const PjOut pj = T.pjs[o];
@@ -110,24 +133,30 @@ __global__ void __launch_bounds__(kPjTile) k_project(DevTables T, PjList L) {
   const int64_t st[3] = {(int64_t)pj.d1 * pj.d2, pj.d2, 1};
   const int l = pj.leg;
   const int d = dd[l];
-  const int e = (tile - pj.tile0) * kPjTile + threadIdx.x;
-  if (e >= d * d) return;
-  const int xp = e / d, x = e % d;
+  const int e = (tile - pj.tile0) * kPjTile + lane;
   const int la = l == 0 ? 1 : 0, lb = l == 2 ? 1 : 2;  // the two other legs
-  const double2* __restrict__ U = T.bufs[pj.u_buf] + (int64_t)xp * st[l];
-  const double2* __restrict__ W = T.bufs[pj.w_buf] + (int64_t)x * st[l];
+  const int nrest = dd[la] * dd[lb];
   double2 acc = make_double2(0.0, 0.0);
-  for (int a = 0; a < dd[la]; ++a)
-    for (int b = 0; b < dd[lb]; ++b) {
-      const int64_t off = (int64_t)a * st[la] + (int64_t)b * st[lb];
+  if (e < d * d) {
+    const int xp = e / d, x = e % d;
+    const double2* __restrict__ U = T.bufs[pj.u_buf] + (int64_t)xp * st[l];
+    const double2* __restrict__ W = T.bufs[pj.w_buf] + (int64_t)x * st[l];
+    for (int r = wid; r < nrest; r += kPjWarps) {
+      const int64_t off = (int64_t)(r / dd[lb]) * st[la] + (int64_t)(r % dd[lb]) * st[lb];
       acc = cfma_conj(U[off], W[off], acc);
     }
+  }
+  part[wid][lane] = acc;
+  __syncthreads();
+  if (wid != 0 || e >= d * d) return;
+  acc = part[0][lane];
+  for (int w = 1; w < kPjWarps; ++w) acc = cadd(acc, part[w][lane]);
   T.mats[pj.dst_mat][e] = acc;
 }
 
 void launch_project(const DevTables& T, const PjList& L, cudaStream_t s) {
   if (L.n_tiles <= 0) return;
-  k_project<<<L.n_tiles, kPjTile, 0, s>>>(T, L);
+  k_project<<<L.n_tiles, 32 * kPjWarps, 0, s>>>(T, L);
 }
 
 // ---------------------------------------------------------------------------
@@ -282,6 +311,7 @@ __global__ void __launch_bounds__(kQrThreads) k_qr(double2* U, int d0, int d1, i
 
 void launch_qr(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work,
                double2* qbuf, double2* R, int* flag, cudaStream_t s) {
+  if (launch_qr_cluster(U, d0, d1, d2, leg, tol, R, flag, s)) return;
   k_qr<<<1, kQrThreads, 0, s>>>(U, d0, d1, d2, leg, tol, work, qbuf, R, flag);
 }
 

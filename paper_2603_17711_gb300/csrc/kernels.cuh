@@ -48,6 +48,11 @@ void launch_project(const DevTables& T, const PjList& L, cudaStream_t s);
 // leaves U unchanged.
 void launch_qr(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work,
                double2* qbuf, double2* R, int* flag, cudaStream_t s);
+// Cluster-parallel variant (qr.cu); returns false when the shape does not fit
+// (bond dim > kQrClusterMaxN or the row blocks exceed shared memory).
+constexpr int kQrClusterMaxN = 64;
+bool launch_qr_cluster(double2* U, int d0, int d1, int d2, int leg, double tol, double2* R, int* flag,
+                       cudaStream_t s);
 void launch_copy(double2* dst, const double2* src, int64_t n, cudaStream_t s);
 // rho / vector contraction for one node: out[a] (non-root) or out[i*d1+j] (root)
 // = sum U[...] w1[.] w2[.] (w = nullptr means the n = 0 unit vector).

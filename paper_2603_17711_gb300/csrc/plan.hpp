@@ -206,7 +206,7 @@ struct Plan {
                   std::vector<std::array<int, 4>>& pairs) const;
 };
 
-constexpr int kApTile = 128;  // elements per CTA of the apply kernel
-constexpr int kPjTile = 128;  // outputs per CTA of the projection kernel
+constexpr int kApTile = 32;   // output elements per CTA of the apply kernel
+constexpr int kPjTile = 32;   // output entries per CTA of the projection kernel
 
 }  // namespace ttn
