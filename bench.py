@@ -146,12 +146,14 @@ def make_gpu(pkg, w, device):
                           drives=w.drives, device=device)
 
 
-def timed_steps(torch, g, w, K, flush, stream):
+def timed_steps(torch, g, w, K, flush):
     """K single steps, each bracketed by CUDA events on the library's stream,
     with an L2 flush (write of 256 MB) between them outside the events."""
     total = 0.0
+    stream = g.stream
     for _ in range(K):
-        flush.zero_()
+        with torch.cuda.stream(stream):
+            flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -167,7 +169,6 @@ def bench_ours(args, rank, world, local_rank):
     import paper_2603_17711_gb300 as pkg
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    stream = torch.cuda.current_stream(dev)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -185,7 +186,7 @@ def bench_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
         wall0 = time.perf_counter()
-        ms = timed_steps(torch, g, w, args.steps, flush, stream)
+        ms = timed_steps(torch, g, w, args.steps, flush)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
     if dist:
@@ -201,7 +202,7 @@ def bench_ours(args, rank, world, local_rank):
     # ---- per-kernel-class device time (roofline of the dominant kernel) ----
     g.ttn_stats_reset()
     g.ttn_profile(True)
-    timed_steps(torch, g, w, args.steps, flush, stream)
+    timed_steps(torch, g, w, args.steps, flush)
     g.ttn_profile(False)
     prof = {k: (g.ttn_stats(k)[0], g.ttn_stats(k)[1], g.ttn_profile_read(k)) for k in range(4)}
     rho_gpu_final = g.ttn_rdm()

@@ -103,7 +103,9 @@ class TTN:
         return int(n.value)
 
     def bind(self, device: int = 0, stream=None) -> None:
-        """Allocate the workspace with PyTorch on ``device`` and bind it (ttn_set_stream + ttn_set_workspace)."""
+        """Allocate the workspace with PyTorch on ``device`` and bind it (ttn_set_stream +
+        ttn_set_workspace). ``stream``: a torch.cuda.Stream for all device work
+        (default: a new stream owned by this object; use ``self.stream``)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("TTN needs a CUDA device: the library has no CPU path")
@@ -112,10 +114,16 @@ class TTN:
         self._ws = torch.empty(n + 256, dtype=torch.uint8, device=dev)
         base = self._ws.data_ptr()
         aligned = (base + 255) // 256 * 256
-        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        # a dedicated stream by default: the legacy default stream cannot be
+        # captured into the per-step CUDA graph
+        s = stream if stream is not None else torch.cuda.Stream(dev)
         self._stream = s
         self._check(self.lib.ttn_set_stream(self.h, C.c_void_p(s.cuda_stream)), "ttn_set_stream")
         self._check(self.lib.ttn_set_workspace(self.h, C.c_void_p(aligned), n), "ttn_set_workspace")
+
+    @property
+    def stream(self):
+        return self._stream
 
     def ttn_set_rdo0(self, rho0: np.ndarray) -> None:
         r = np.ascontiguousarray(np.asarray(rho0, np.complex128)).view(np.float64)

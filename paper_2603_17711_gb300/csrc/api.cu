@@ -68,7 +68,19 @@ struct ttn_ctx {
   std::vector<Mark> marks;
   double prof_ms[4] = {0, 0, 0, 0};
 
+  // one ps1 step captured as a CUDA graph (autonomous generators, non-default stream)
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0.0;
+  bool graph_disabled = false;
+  int64_t graph_launch[4] = {0, 0, 0, 0};
+  double graph_flops[4] = {0, 0, 0, 0};
+  void drop_graph() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+  }
+
   ~ttn_ctx() {
+    drop_graph();
     for (auto& m : marks) {
       cudaEventDestroy(m.a);
       cudaEventDestroy(m.b);
@@ -407,6 +419,7 @@ ttn_status ttn_set_params(ttn_t h, const ttn_params* prm) {
     if (h->ws_bound && prm->max_rank != h->params.max_rank)
       return h->fail(TTN_ESTATE, "max_rank must be set before the workspace is bound");
     h->params = *prm;
+    h->drop_graph();  // substep counts and tolerances are baked into a captured step
     return TTN_OK;
   });
 }
@@ -465,6 +478,7 @@ ttn_status ttn_workspace_size(ttn_t h, size_t* bytes) {
 ttn_status ttn_set_stream(ttn_t h, void* stream) {
   if (!h) return TTN_EINVAL;
   h->stream = (cudaStream_t)stream;
+  h->drop_graph();
   return TTN_OK;
 }
 
@@ -601,7 +615,50 @@ ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
     ttn_status st = ensure_envs(h);
     if (st != TTN_OK) return st;
     Exec ex(h);
-    for (int k = 0; k < n_steps; ++k) {
+    int k = 0;
+    const bool graphable = h->plan.n_drives == 0 && !h->profiling && h->stream != nullptr && !h->graph_disabled;
+    if (graphable && n_steps > 0 && (!h->graph || h->graph_dt != dt)) {
+      // capture one step; the launches recorded while capturing do not run
+      h->drop_graph();
+      int64_t l0[4];
+      double f0[4];
+      for (int c = 0; c < 4; ++c) {
+        l0[c] = h->n_launch[c];
+        f0[c] = h->n_flops[c];
+      }
+      cudaGraph_t g = nullptr;
+      bool ok = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        ex.step_ps1(dt, h->t);
+        ok = cudaStreamEndCapture(h->stream, &g) == cudaSuccess && g != nullptr;
+      }
+      if (ok) ok = cudaGraphInstantiate(&h->graph, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+      for (int c = 0; c < 4; ++c) {
+        h->graph_launch[c] = h->n_launch[c] - l0[c];
+        h->graph_flops[c] = h->n_flops[c] - f0[c];
+        h->n_launch[c] = l0[c];
+        h->n_flops[c] = f0[c];
+      }
+      if (!ok) {
+        cudaGetLastError();  // clear the capture error; run this call without a graph
+        h->drop_graph();
+        h->graph_disabled = true;
+      } else {
+        h->graph_dt = dt;
+      }
+    }
+    if (graphable && h->graph) {
+      for (; k < n_steps; ++k) {
+        CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+        for (int c = 0; c < 4; ++c) {
+          h->n_launch[c] += h->graph_launch[c];
+          h->n_flops[c] += h->graph_flops[c];
+        }
+        h->t += dt;
+      }
+    }
+    for (; k < n_steps; ++k) {
       ex.step_ps1(dt, h->t);
       h->t += dt;
     }

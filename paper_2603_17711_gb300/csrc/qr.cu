@@ -118,10 +118,10 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
   fro = bsum(fro, red);
   if (tid == 0) s_part[0] = fro;
   cluster.sync();
-  if (tid == 0) {
-    double s = 0.0;
-    for (int c = 0; c < C; ++c) s += *cluster.map_shared_rank(&s_part[0], c);
-    s_bcast[0] = sqrt(s);
+  if (wid == 0) {  // lane c reads CTA c's partial; fixed butterfly order
+    double v = lane < C ? *cluster.map_shared_rank(&s_part[0], lane) : 0.0;
+    v = wsum(v);
+    if (lane == 0) s_bcast[0] = sqrt(v);
   }
   __syncthreads();
   const double frob = s_bcast[0];
@@ -146,11 +146,13 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
       if (owner == me) s_x0[par] = x[j - r0];
     }
     cluster.sync();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int c = 0; c < C; ++c) s += *cluster.map_shared_rank(&s_part[par], c);
-      s_bcast[1] = sqrt(s);
-      s_bx0 = *cluster.map_shared_rank(&s_x0[par], owner);
+    if (wid == 0) {
+      double v = lane < C ? *cluster.map_shared_rank(&s_part[par], lane) : 0.0;
+      v = wsum(v);
+      if (lane == 0) {
+        s_bcast[1] = sqrt(v);
+        s_bx0 = *cluster.map_shared_rank(&s_x0[par], owner);
+      }
     }
     __syncthreads();
     const double alpha = s_bcast[1];
@@ -231,11 +233,14 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
   cluster.sync();
   // full Gram (fixed order over CTAs) into T's storage temporarily
   for (int k = tid; k < n * n; k += nt) {
+    double2 v[16];  // all remote loads in flight before the fixed-order sum
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = c < C ? cluster.map_shared_rank(G, c)[k] : make_double2(0.0, 0.0);
     double2 g = make_double2(0.0, 0.0);
-    for (int c = 0; c < C; ++c) {
-      const double2 p = cluster.map_shared_rank(G, c)[k];
-      g.x += p.x;
-      g.y += p.y;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      g.x += v[c].x;
+      g.y += v[c].y;
     }
     T[k] = g;
   }
