@@ -154,8 +154,11 @@ ttn_status ttn_set_rdo0(ttn_t h, const double* rho0);
 /* Advance n_steps steps of length dt with scheme TTN_PS1 or TTN_PS2 (one step =
  * the symmetric composition of a half sweep over dt/2 and its adjoint). The
  * orthogonality centre is at the root before and after. Asynchronous on the
- * handle's stream except for drive sampling on the host. TTN_ENUMERIC if a
- * non-finite amplitude appeared (checked once per call). */
+ * handle's stream except for drive sampling on the host. For an autonomous
+ * generator on a non-default stream the kernels of one ps1 step are captured
+ * once as a CUDA graph (per dt) and replayed. A non-finite amplitude is
+ * detected on the device once per call and reported as TTN_ENUMERIC by the
+ * next synchronising call (ttn_rdm, ttn_get_node). */
 ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps);
 
 /* rho_S = <0|Omega>: contract every feature leg with the n = 0 vector.
@@ -196,6 +199,30 @@ ttn_status ttn_stats(ttn_t h, int32_t kind, int64_t* launches, double* flops);
 ttn_status ttn_profile(ttn_t h, int32_t on);
 ttn_status ttn_profile_read(ttn_t h, int32_t kind, double* ms);
 ttn_status ttn_stats_reset(ttn_t h);
+
+/* No-allocation RDM. The paper has no counterpart to this entry point; it is
+ * a deployment aid. Some callers cannot allocate device memory at all: code
+ * running inside another framework's memory pool or arena, or runtimes that
+ * forbid allocation once they have started. Such a caller cannot give a handle
+ * its workspace, so this call takes node tensors the caller already holds in
+ * device memory and computes rho_S = <0|Omega> into rho_dev (M*M complex,
+ * row-major) without allocating anything: its only scratch, one contraction
+ * vector per node (the sum of all bond ranks, at most 65536 complex values), is
+ * a fixed 1 MiB array compiled into the library, which every GPU that loads the
+ * library keeps until the process exits. A tree needing more is refused with
+ * TTN_EINVAL and a message in err (err_len bytes; err may be NULL).
+ * node_dev[u] points to node u's tensor in canonical layout (the layout
+ * ttn_get_node returns); tree, leg_dims and ranks are as for ttn_create. The
+ * first call on each device looks up the array's device address with that
+ * device current; make that first call before any CUDA stream capture. All
+ * calls on one device share the array, which keeps the last call's contents;
+ * every entry a call reads it has written first, so nothing needs clearing.
+ * Calls that overlap on the GPU (different streams or host threads) race on
+ * the array. Work is issued on `stream` (a cudaStream_t passed as void*); the
+ * call does not synchronise. */
+ttn_status ttn_rdm_noalloc(const ttn_tree* tree, const int32_t* leg_dims, const int32_t* ranks,
+                           const void* const* node_dev, void* rho_dev, void* stream, char* err,
+                           size_t err_len);
 
 const char* ttn_last_error(ttn_t h);
 void ttn_destroy(ttn_t h);
