@@ -141,9 +141,9 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # GPU leg
 # ----------------------------------------------------------------------------
-def make_gpu(pkg, w, device):
+def make_gpu(pkg, w, device, precision=0):
     return pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0,
-                          drives=w.drives, device=device)
+                          drives=w.drives, device=device, precision=precision)
 
 
 def timed_steps(torch, g, w, K, flush):
@@ -208,6 +208,32 @@ def bench_ours(args, rank, world, local_rank):
     rho_gpu_final = g.ttn_rdm()
     g.close()
 
+    # ---- mixed-precision form on the same workload (FP32 contractions) ----
+    gm = make_gpu(pkg, w, local_rank, precision=pkg.TTN_MIXED_FP32)
+    for _ in range(args.warmup):
+        gm.ttn_step(w.dt, 1, 1)
+    torch.cuda.synchronize()
+    gm.ttn_stats_reset()
+    ms_mixed = timed_steps(torch, gm, w, args.steps, flush)
+    mixed_flops = gm.ttn_stats(0)[1]
+    gm.ttn_stats_reset()
+    gm.ttn_profile(True)
+    timed_steps(torch, gm, w, args.steps, flush)
+    gm.ttn_profile(False)
+    prof_m = {k: (gm.ttn_stats(k)[0], gm.ttn_stats(k)[1], gm.ttn_profile_read(k)) for k in range(4)}
+    gm.close()
+    # accuracy of the mixed form against the FP64 form over the same steps
+    ga = make_gpu(pkg, w, local_rank)
+    gb = make_gpu(pkg, w, local_rank, precision=pkg.TTN_MIXED_FP32)
+    mixed_err = 0.0
+    n_cmp = args.warmup + 2 * args.steps
+    for _ in range(n_cmp):
+        ga.ttn_step(w.dt, 1, 1)
+        gb.ttn_step(w.dt, 1, 1)
+        mixed_err = max(mixed_err, float(np.max(np.abs(ga.ttn_rdm() - gb.ttn_rdm()))))
+    ga.close()
+    gb.close()
+
     # ---- end to end through the public API with host buffers ----
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -250,6 +276,14 @@ def bench_ours(args, rank, world, local_rank):
                              "share_of_step_time": k1_ms / (ms_max if ms_max > 0 else 1)},
         "kernel_time_share": {names[k]: prof[k][2] / sum(p[2] for p in prof.values()) for k in range(4)},
         "plain_fp64_steps_per_s": value,
+        "mixed_fp32": {"steps_per_s": world * args.steps / (ms_mixed * 1e-3),
+                       "speedup_vs_plain_fp64": ms_max / ms_mixed,
+                       "rdm_max_abs_vs_fp64_gpu": mixed_err, "steps_compared": n_cmp,
+                       "node_contraction_tflops_kernel": (prof_m[0][1] / (prof_m[0][2] * 1e-3) / 1e12)
+                       if prof_m[0][2] > 0 else None,
+                       "node_contraction_gflop_per_step": mixed_flops / args.steps / 1e9,
+                       "kernel_time_share": {names[k]: prof_m[k][2] / sum(p[2] for p in prof_m.values())
+                                             for k in range(4)}},
         "e2e": {"value": world * args.steps / e2e_s, "unit": "steps/s",
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 16 * w.M * w.M,
                 "includes": "handle build, sop_load, workspace bind, rho0 upload, K steps with rho_S read back each step"},

@@ -44,9 +44,12 @@ struct ttn_ctx {
   // workspace
   char* ws = nullptr;
   size_t ws_bytes = 0;
-  std::vector<double2*> h_bufs;  // device addresses per buffer id
-  std::vector<double2*> h_mats;  // device addresses per matrix id
+  std::vector<double2*> h_bufs;  // FP64 device addresses per buffer id
+  std::vector<double2*> h_mats;  // FP64 device addresses per matrix id
+  std::vector<void*> h_bufs_lo;  // contraction-type addresses (== h_bufs in FP64 mode)
+  std::vector<void*> h_mats_lo;
   double2* pool = nullptr;
+  int prec = PREC_F64;
   double2* qr_work = nullptr;
   double2* rdm_vec = nullptr;
   double2* rho_dev = nullptr;
@@ -54,7 +57,8 @@ struct ttn_ctx {
   DriveMat* drive_list_dev = nullptr;
   std::vector<DriveMat> drive_list;
   std::vector<int64_t> rdm_off;  // per node offset into rdm_vec
-  DevTables T{};
+  DevTables T{};    // FP64 table (absorb; everything in FP64 mode)
+  DevTables Tlo{};  // contraction table (== T in FP64 mode)
 
   // kernel accounting (ttn_stats / ttn_profile)
   int64_t n_launch[4] = {0, 0, 0, 0};
@@ -135,12 +139,13 @@ ttn_status cuda_fail(ttn_t h, cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 struct Layout {
   size_t nodes, pool, scratch, qr, rdm, rho, bufs_tab, mats_tab, terms, outs, pjs, drives, flag, total;
+  size_t nodes32 = 0, pool32 = 0, scratch32 = 0, bufs_tab_lo = 0, mats_tab_lo = 0;  // FP32 mode only
   std::vector<int64_t> node_off;  // complex elements from `nodes`
   std::vector<int64_t> rdm_off;
   int64_t scratch_elems = 0, qr_elems = 0, rdm_elems = 0;
 };
 
-Layout layout_of(const Plan& p) {
+Layout layout_of(const Plan& p, int prec) {
   Layout L;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -179,6 +184,14 @@ Layout layout_of(const Plan& p) {
   L.pjs = take(p.pj_outs.size() * sizeof(PjOut));
   L.drives = take(p.locals.size() * sizeof(DriveMat));
   L.flag = take(sizeof(int) * 4);
+  if (prec == PREC_F32) {
+    L.nodes32 = take(acc * sizeof(float2));
+    L.pool32 = take(std::max<int64_t>(p.mat_pool, 1) * sizeof(float2));
+    // ys, T_g, W_c and the bond shadow / stage input in FP32
+    L.scratch32 = take(((int64_t)(1 + p.buf.n_t + p.buf.n_w) * p.P_max + 2 * r2) * sizeof(float2));
+    L.bufs_tab_lo = take(p.buf.n_bufs * sizeof(void*));
+    L.mats_tab_lo = take(p.mats.size() * sizeof(void*));
+  }
   L.total = off;
   return L;
 }
@@ -212,9 +225,9 @@ struct Exec {
   void apply(int kind, int list, const Epi& e) {
     if (list < 0) return;
     const ApList& L = p.ap_lists[list];
-    run(kind, L.flops, [&] { launch_apply(h->T, L, e, s); });
+    run(kind, L.flops, [&] { launch_apply(h->prec, h->Tlo, L, e, s); });
   }
-  void store(int kind, int list) { apply(kind, list, Epi{EPI_STORE, 0, 0, 0, 0.0}); }
+  void store(int kind, int list) { apply(kind, list, Epi{EPI_STORE, nullptr, nullptr, nullptr, nullptr, 0.0}); }
 
   void env(int a, int b) {
     const EnvLists& E = p.env[p.dir_id(a, b)];
@@ -222,7 +235,7 @@ struct Exec {
     store(1, E.classes);
     if (E.project >= 0) {
       const PjList& L = p.pj_lists[E.project];
-      run(1, L.flops, [&] { launch_project(h->T, L, s); });
+      run(1, L.flops, [&] { launch_project(h->prec, h->Tlo, L, s); });
     }
   }
   // U_u := Q (semi-unitary toward neighbour v), R -> bond buffer
@@ -234,14 +247,19 @@ struct Exec {
     const double flops = 8.0 * 2.0 * (2.0 * m * n * n - 2.0 * n * n * n / 3.0);
     run(2, flops, [&] {
       launch_qr(h->h_bufs[u], d[0], d[1], d[2], li, h->params.qr_tol, h->qr_work,
-                h->h_bufs[p.buf.tmp], h->h_bufs[p.buf.bond_y], h->flag_dev, s);
+                h->h_bufs[p.buf.tmp], h->h_bufs[p.buf.bond_y], h->flag_dev, lo_copy(u), lo_copy(p.buf.bond_y), s);
     });
   }
-  // U_v := R x_(leg of v facing u) U_v
+  // FP32 shadow of an FP64 buffer (nullptr in FP64 mode, where they coincide)
+  float2* lo_copy(int buf) { return h->prec == PREC_F32 ? (float2*)h->h_bufs_lo[buf] : nullptr; }
+  // U_v := R x_(leg of v facing u) U_v, in FP64 (a gauge move), shadow refreshed
   void absorb(int v, int u) {
     const int li = p.tree.leg_index(v, u);
-    store(3, p.absorb[v][li]);
-    run(3, 0.0, [&] { launch_copy(h->h_bufs[v], h->h_bufs[p.buf.tmp], p.P[v], s); });
+    const ApList& L = p.ap_lists[p.absorb[v][li]];
+    run(3, L.flops, [&] {
+      launch_apply(PREC_F64, h->T, L, Epi{EPI_STORE, nullptr, nullptr, nullptr, nullptr, 0.0}, s);
+    });
+    run(3, 0.0, [&] { launch_copy(h->h_bufs[v], lo_copy(v), h->h_bufs[p.buf.tmp], p.P[v], s); });
   }
   void rk4(const FlowLists& F, int y, int ys, int acc, double tau) {
     const int m = p.n_sub(tau, h->params.kappa);
@@ -250,7 +268,7 @@ struct Exec {
       for (int st = 1; st <= 4; ++st) {
         const int var = st == 1 ? 0 : 1;
         store(0, F.first[var]);
-        apply(0, F.combine[var], Epi{st, y, ys, acc, hs});
+        apply(0, F.combine[var], Epi{st, h->h_bufs[y], h->h_bufs_lo[y], h->h_bufs_lo[ys], h->h_bufs[acc], hs});
       }
   }
   void node_flow(int u, double tau) { rk4(p.node_flow[u], u, p.buf.ys, p.buf.acc, tau); }
@@ -292,7 +310,10 @@ struct Exec {
     DriveArgs g{};
     for (size_t d = 0; d < h->drives.size() && d < (size_t)kMaxDrives; ++d)
       g.g[d] = h->drives[d].fn ? h->drives[d].fn(t, h->drives[d].user) : 0.0;
-    run(3, 0.0, [&] { launch_drive(h->T.mats, h->drive_list_dev, (int)h->drive_list.size(), g, s); });
+    float2* const* m32 = h->prec == PREC_F32 ? (float2* const*)h->Tlo.mats : nullptr;
+    run(3, 0.0, [&] {
+      launch_drive((double2* const*)h->T.mats, m32, h->drive_list_dev, (int)h->drive_list.size(), g, s);
+    });
   }
   void step_ps1(double dt, double t0) {
     const double hh = 0.5 * dt;
@@ -345,6 +366,20 @@ ttn_status status_of(const std::string& e) {
   return TTN_EINVAL;
 }
 
+// Copy n complex values to an FP64 device buffer and, in FP32 mode, to its shadow.
+ttn_status upload_pair(ttn_t h, double2* dst, void* dst_lo, const double2* src, size_t n) {
+  cudaStream_t s = h->stream;
+  CUDA_TRY(h, cudaMemcpyAsync(dst, src, n * sizeof(double2), cudaMemcpyHostToDevice, s));
+  if (h->prec == PREC_F32 && dst_lo && dst_lo != (void*)dst) {
+    std::vector<float2> lo(n);
+    for (size_t i = 0; i < n; ++i) lo[i] = make_float2((float)src[i].x, (float)src[i].y);
+    CUDA_TRY(h, cudaMemcpyAsync(dst_lo, lo.data(), n * sizeof(float2), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  return TTN_OK;
+}
+
 ttn_status upload_initial(ttn_t h, const double* rho0) {
   Plan& p = h->plan;
   const int M = p.leg_dims[0];
@@ -361,9 +396,10 @@ ttn_status upload_initial(ttn_t h, const double* rho0) {
       const int64_t cols = (int64_t)d[1] * d[2];
       for (int a = 0; a < d[0]; ++a) T[(size_t)a * cols + a] = make_double2(1.0, 0.0);
     }
-    CUDA_TRY(h, cudaMemcpyAsync(h->h_bufs[u], T.data(), T.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(h, cudaStreamSynchronize(s));
+    ttn_status st = upload_pair(h, h->h_bufs[u], h->h_bufs_lo[u], T.data(), T.size());
+    if (st != TTN_OK) return st;
   }
+  (void)s;
   h->envs_dirty = true;
   h->t = 0.0;
   return TTN_OK;
@@ -401,11 +437,8 @@ ttn_status ttn_create(const ttn_tree* tree, const int32_t* leg_dims, const int32
     delete h;
     return st;
   }
-  if (precision != TTN_FP64) {
-    delete h;
-    return TTN_EUNSUPPORTED;
-  }
   h->precision = precision;
+  h->prec = precision == TTN_MIXED_FP32 ? PREC_F32 : PREC_F64;
   *out = h;
   return TTN_OK;
 }
@@ -470,7 +503,7 @@ ttn_status ttn_workspace_size(ttn_t h, size_t* bytes) {
   return guarded(h, [&]() -> ttn_status {
     if (!bytes) return h->fail(TTN_EINVAL, "null bytes");
     if (!h->sop_loaded) return h->fail(TTN_ESTATE, "sop_load first");
-    *bytes = layout_of(h->plan).total;
+    *bytes = layout_of(h->plan, h->prec).total;
     return TTN_OK;
   });
 }
@@ -489,7 +522,7 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
     for (int d = 0; d < h->plan.n_drives; ++d)
       if (!h->drives[d].fn) return h->fail(TTN_ESTATE, "a drive used by the SOP has no function");
     Plan& p = h->plan;
-    Layout L = layout_of(p);
+    Layout L = layout_of(p, h->prec);
     if (bytes < L.total) return h->fail(TTN_ENOMEM, "workspace smaller than ttn_workspace_size");
     char* base = (char*)dptr;
     h->ws = base;
@@ -524,17 +557,53 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
     h->rdm_off = L.rdm_off;
     h->rho_dev = (double2*)(base + L.rho);
     h->flag_dev = (int*)(base + L.flag);
-    h->T.bufs = (double2* const*)(base + L.bufs_tab);
-    h->T.mats = (double2* const*)(base + L.mats_tab);
+    h->T.bufs = (void* const*)(base + L.bufs_tab);
+    h->T.mats = (void* const*)(base + L.mats_tab);
     h->T.terms = (const ApTerm*)(base + L.terms);
     h->T.outs = (const ApOut*)(base + L.outs);
     h->T.pjs = (const PjOut*)(base + L.pjs);
     h->drive_list_dev = (DriveMat*)(base + L.drives);
+    // contraction-type view: FP64 mode aliases the FP64 buffers
+    h->h_bufs_lo.assign(h->h_bufs.begin(), h->h_bufs.end());
+    h->h_mats_lo.assign(h->h_mats.begin(), h->h_mats.end());
+    h->Tlo = h->T;
+    if (h->prec == PREC_F32) {
+      float2* n32 = (float2*)(base + L.nodes32);
+      for (int u = 0; u < p.tree.n_nodes; ++u) h->h_bufs_lo[u] = n32 + L.node_off[u];
+      float2* sc = (float2*)(base + L.scratch32);
+      int64_t o32 = 0;
+      auto nx = [&](int64_t n) {
+        float2* q = sc + o32;
+        o32 += n;
+        return (void*)q;
+      };
+      h->h_bufs_lo[p.buf.ys] = nx(p.P_max);
+      for (int i = 0; i < p.buf.n_t; ++i) h->h_bufs_lo[p.buf.t0 + i] = nx(p.P_max);
+      for (int i = 0; i < p.buf.n_w; ++i) h->h_bufs_lo[p.buf.w0 + i] = nx(p.P_max);
+      h->h_bufs_lo[p.buf.bond_y] = nx(r2);
+      h->h_bufs_lo[p.buf.bond_ys] = nx(r2);
+      h->h_bufs_lo[p.buf.acc] = nullptr;       // accumulators stay FP64 (epilogue pointers)
+      h->h_bufs_lo[p.buf.bond_acc] = nullptr;
+      h->h_bufs_lo[p.buf.tmp] = nullptr;       // absorb runs in FP64
+      float2* p32 = (float2*)(base + L.pool32);
+      for (size_t i = 0; i < p.mats.size(); ++i)
+        h->h_mats_lo[i] = p.mats[i].off >= 0 ? (void*)(p32 + p.mats[i].off) : nullptr;
+      h->h_mats_lo[p.bond_mat] = h->h_bufs_lo[p.buf.bond_y];
+      h->Tlo.bufs = (void* const*)(base + L.bufs_tab_lo);
+      h->Tlo.mats = (void* const*)(base + L.mats_tab_lo);
+    }
     cudaStream_t s = h->stream;
     CUDA_TRY(h, cudaMemcpyAsync((void*)h->T.bufs, h->h_bufs.data(), h->h_bufs.size() * sizeof(double2*),
                                 cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaMemcpyAsync((void*)h->T.mats, h->h_mats.data(), h->h_mats.size() * sizeof(double2*),
                                 cudaMemcpyHostToDevice, s));
+    if (h->prec == PREC_F32) {
+      CUDA_TRY(h, cudaMemcpyAsync((void*)h->Tlo.bufs, h->h_bufs_lo.data(), h->h_bufs_lo.size() * sizeof(void*),
+                                  cudaMemcpyHostToDevice, s));
+      CUDA_TRY(h, cudaMemcpyAsync((void*)h->Tlo.mats, h->h_mats_lo.data(), h->h_mats_lo.size() * sizeof(void*),
+                                  cudaMemcpyHostToDevice, s));
+      CUDA_TRY(h, cudaStreamSynchronize(s));
+    }
     if (!p.ap_terms.empty())
       CUDA_TRY(h, cudaMemcpyAsync((void*)h->T.terms, p.ap_terms.data(), p.ap_terms.size() * sizeof(ApTerm),
                                   cudaMemcpyHostToDevice, s));
@@ -547,11 +616,18 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
     // open-leg matrices: current = static part at g = 0; drive parts
     h->drive_list.clear();
     std::vector<double2> tmp;
+    std::vector<float2> tmp32;
     auto put = [&](int slot, const std::vector<cd>& m) -> cudaError_t {
       tmp.resize(m.size());
       for (size_t i = 0; i < m.size(); ++i) tmp[i] = make_double2(m[i].real(), m[i].imag());
       cudaError_t e = cudaMemcpyAsync(h->h_mats[slot], tmp.data(), tmp.size() * sizeof(double2),
                                       cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess && h->prec == PREC_F32 && h->h_mats_lo[slot] != (void*)h->h_mats[slot]) {
+        tmp32.resize(m.size());
+        for (size_t i = 0; i < m.size(); ++i) tmp32[i] = make_float2((float)m[i].real(), (float)m[i].imag());
+        e = cudaMemcpyAsync(h->h_mats_lo[slot], tmp32.data(), tmp32.size() * sizeof(float2),
+                            cudaMemcpyHostToDevice, s);
+      }
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       return e;
     };
@@ -730,9 +806,8 @@ ttn_status ttn_set_node(ttn_t h, int32_t u, const double* host_in) {
     if (u < 0 || u >= h->plan.tree.n_nodes || !host_in) return h->fail(TTN_EINVAL, "bad node or input");
     for (int64_t i = 0; i < 2 * h->plan.P[u]; ++i)
       if (!std::isfinite(host_in[i])) return h->fail(TTN_EINVAL, "non-finite node entry");
-    CUDA_TRY(h, cudaMemcpyAsync(h->h_bufs[u], host_in, h->plan.P[u] * sizeof(double2), cudaMemcpyHostToDevice,
-                                h->stream));
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    ttn_status st = upload_pair(h, h->h_bufs[u], h->h_bufs_lo[u], (const double2*)host_in, (size_t)h->plan.P[u]);
+    if (st != TTN_OK) return st;
     h->envs_dirty = true;
     return TTN_OK;
   });

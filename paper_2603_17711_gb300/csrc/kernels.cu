@@ -28,20 +28,58 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
 
 // ---------------------------------------------------------------------------
+// Complex arithmetic in the contraction type (double2 or float2).
+// ---------------------------------------------------------------------------
+template <typename R> struct Cx;
+template <> struct Cx<double> {
+  using T = double2;
+  __device__ static T zero() { return make_double2(0.0, 0.0); }
+  __device__ static T fma(T a, T b, T c) { return cfma(a, b, c); }
+  __device__ static T fmaj(T a, T b, T c) { return cfma_conj(a, b, c); }
+  __device__ static T add(T a, T b) { return cadd(a, b); }
+  __device__ static double2 wide(T a) { return a; }
+  __device__ static T narrow(double2 a) { return a; }
+};
+template <> struct Cx<float> {
+  using T = float2;
+  __device__ static T zero() { return make_float2(0.f, 0.f); }
+  __device__ static T fma(T a, T b, T c) {
+    c.x = fmaf(a.x, b.x, c.x);
+    c.x = fmaf(-a.y, b.y, c.x);
+    c.y = fmaf(a.x, b.y, c.y);
+    c.y = fmaf(a.y, b.x, c.y);
+    return c;
+  }
+  __device__ static T fmaj(T a, T b, T c) {
+    c.x = fmaf(a.x, b.x, c.x);
+    c.x = fmaf(a.y, b.y, c.x);
+    c.y = fmaf(a.x, b.y, c.y);
+    c.y = fmaf(-a.y, b.x, c.y);
+    return c;
+  }
+  __device__ static T add(T a, T b) { return make_float2(a.x + b.x, a.y + b.y); }
+  __device__ static double2 wide(T a) { return make_double2(a.x, a.y); }
+  __device__ static T narrow(double2 a) { return make_float2((float)a.x, (float)a.y); }
+};
+
+// ---------------------------------------------------------------------------
 // Sum of mode products: out_o[idx] = sum_t M_t x_{leg_t} src_t.
 // A CTA owns 32 consecutive output elements (one per lane); its 8 warps split
 // the term list (warp w takes terms w, w+8, ...) and the partial sums are
 // added in a fixed order in shared memory, so results are bitwise
-// reproducible. FP64 issue (~2 FMA/clk/SM) is the bound: the mapping spreads
-// a node application over as many SMs as possible.
+// reproducible. In FP64 the bound is FP64 issue (~2 FMA/clk/SM): the mapping
+// spreads a node application over as many SMs as possible.
 // ---------------------------------------------------------------------------
 constexpr int kApWarps = 8;
 
-__device__ __forceinline__ double2 term_dot(const ApTerm& term, const DevTables& T, int64_t idx, int i0, int i1,
-                                            int i2, int d0, int d1, int d2) {
-  const double2* __restrict__ src = T.bufs[term.src];
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::T term_dot(const ApTerm& term, const DevTables& T, int64_t idx,
+                                                      int i0, int i1, int i2, int d0, int d1, int d2) {
+  using C = Cx<R>;
+  using V = typename C::T;
+  const V* __restrict__ src = (const V*)T.bufs[term.src];
   if (term.mat < 0) return src[idx];
-  const double2* __restrict__ M = T.mats[term.mat];
+  const V* __restrict__ M = (const V*)T.mats[term.mat];
   int dl, il;
   int64_t stride;
   if (term.leg == 0) {
@@ -51,15 +89,18 @@ __device__ __forceinline__ double2 term_dot(const ApTerm& term, const DevTables&
   } else {
     dl = d2; il = i2; stride = 1;
   }
-  const double2* __restrict__ row = M + (int64_t)il * dl;
-  const double2* __restrict__ col = src + (idx - (int64_t)il * stride);
-  double2 acc = make_double2(0.0, 0.0);
-  for (int x = 0; x < dl; ++x) acc = cfma(row[x], col[(int64_t)x * stride], acc);
+  const V* __restrict__ row = M + (int64_t)il * dl;
+  const V* __restrict__ col = src + (idx - (int64_t)il * stride);
+  V acc = C::zero();
+  for (int x = 0; x < dl; ++x) acc = C::fma(row[x], col[(int64_t)x * stride], acc);
   return acc;
 }
 
+template <typename R>
 __global__ void __launch_bounds__(32 * kApWarps) k_apply(DevTables T, ApList L, Epi ep) {
-  __shared__ double2 part[kApWarps][32];
+  using C = Cx<R>;
+  using V = typename C::T;
+  __shared__ V part[kApWarps][32];
   const int tile = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int o = L.out_begin;
@@ -68,51 +109,56 @@ __global__ void __launch_bounds__(32 * kApWarps) k_apply(DevTables T, ApList L, 
   const int d0 = out.d0, d1 = out.d1, d2 = out.d2;
   const int64_t P = (int64_t)d0 * d1 * d2;
   const int64_t idx = (int64_t)(tile - out.tile0) * kApTile + lane;
-  double2 acc = make_double2(0.0, 0.0);
+  V acc = C::zero();
   if (idx < P) {
     const int i2 = (int)(idx % d2);
     const int i1 = (int)((idx / d2) % d1);
     const int i0 = (int)(idx / ((int64_t)d1 * d2));
-    for (int t = out.term_begin + wid; t < out.term_end; t += kApWarps) {
-      const double2 v = term_dot(T.terms[t], T, idx, i0, i1, i2, d0, d1, d2);
-      acc = cadd(acc, v);
-    }
+    for (int t = out.term_begin + wid; t < out.term_end; t += kApWarps)
+      acc = C::add(acc, term_dot<R>(T.terms[t], T, idx, i0, i1, i2, d0, d1, d2));
   }
   part[wid][lane] = acc;
   __syncthreads();
   if (wid != 0 || idx >= P) return;
   acc = part[0][lane];
-  for (int w = 1; w < kApWarps; ++w) acc = cadd(acc, part[w][lane]);
+  for (int w = 1; w < kApWarps; ++w) acc = C::add(acc, part[w][lane]);
   if (ep.mode == EPI_STORE) {
-    T.bufs[out.dst][idx] = acc;
+    ((V*)T.bufs[out.dst])[idx] = acc;
     return;
   }
-  double2* __restrict__ y = T.bufs[ep.y];
-  double2* __restrict__ ys = T.bufs[ep.ys];
-  double2* __restrict__ ac = T.bufs[ep.acc];
+  const double2 k = C::wide(acc);
+  double2* __restrict__ y = ep.y;
+  double2* __restrict__ ac = ep.acc;
+  V* __restrict__ ys = (V*)ep.ys;
   const double h = ep.h;
   switch (ep.mode) {
     case EPI_RK1:
-      ac[idx] = acc;
-      ys[idx] = cadd(y[idx], cscale(0.5 * h, acc));
+      ac[idx] = k;
+      ys[idx] = C::narrow(cadd(y[idx], cscale(0.5 * h, k)));
       break;
     case EPI_RK2:
-      ac[idx] = cadd(ac[idx], cscale(2.0, acc));
-      ys[idx] = cadd(y[idx], cscale(0.5 * h, acc));
+      ac[idx] = cadd(ac[idx], cscale(2.0, k));
+      ys[idx] = C::narrow(cadd(y[idx], cscale(0.5 * h, k)));
       break;
     case EPI_RK3:
-      ac[idx] = cadd(ac[idx], cscale(2.0, acc));
-      ys[idx] = cadd(y[idx], cscale(h, acc));
+      ac[idx] = cadd(ac[idx], cscale(2.0, k));
+      ys[idx] = C::narrow(cadd(y[idx], cscale(h, k)));
       break;
-    default:
-      y[idx] = cadd(y[idx], cscale(h / 6.0, cadd(ac[idx], acc)));
+    default: {
+      const double2 yn = cadd(y[idx], cscale(h / 6.0, cadd(ac[idx], k)));
+      y[idx] = yn;
+      if ((void*)ep.y_lo != (void*)ep.y) ((V*)ep.y_lo)[idx] = C::narrow(yn);
       break;
+    }
   }
 }
 
-void launch_apply(const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s) {
+void launch_apply(int prec, const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s) {
   if (L.n_tiles <= 0) return;
-  k_apply<<<L.n_tiles, 32 * kApWarps, 0, s>>>(T, L, e);
+  if (prec == PREC_F32)
+    k_apply<float><<<L.n_tiles, 32 * kApWarps, 0, s>>>(T, L, e);
+  else
+    k_apply<double><<<L.n_tiles, 32 * kApWarps, 0, s>>>(T, L, e);
 }
 
 // ---------------------------------------------------------------------------
@@ -122,8 +168,11 @@ void launch_apply(const DevTables& T, const ApList& L, const Epi& e, cudaStream_
 // ---------------------------------------------------------------------------
 constexpr int kPjWarps = 8;
 
+template <typename R>
 __global__ void __launch_bounds__(32 * kPjWarps) k_project(DevTables T, PjList L) {
-  __shared__ double2 part[kPjWarps][32];
+  using C = Cx<R>;
+  using V = typename C::T;
+  __shared__ V part[kPjWarps][32];
   const int tile = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int o = L.out_begin;
@@ -136,27 +185,30 @@ __global__ void __launch_bounds__(32 * kPjWarps) k_project(DevTables T, PjList L
   const int e = (tile - pj.tile0) * kPjTile + lane;
   const int la = l == 0 ? 1 : 0, lb = l == 2 ? 1 : 2;  // the two other legs
   const int nrest = dd[la] * dd[lb];
-  double2 acc = make_double2(0.0, 0.0);
+  V acc = C::zero();
   if (e < d * d) {
     const int xp = e / d, x = e % d;
-    const double2* __restrict__ U = T.bufs[pj.u_buf] + (int64_t)xp * st[l];
-    const double2* __restrict__ W = T.bufs[pj.w_buf] + (int64_t)x * st[l];
+    const V* __restrict__ U = (const V*)T.bufs[pj.u_buf] + (int64_t)xp * st[l];
+    const V* __restrict__ W = (const V*)T.bufs[pj.w_buf] + (int64_t)x * st[l];
     for (int r = wid; r < nrest; r += kPjWarps) {
       const int64_t off = (int64_t)(r / dd[lb]) * st[la] + (int64_t)(r % dd[lb]) * st[lb];
-      acc = cfma_conj(U[off], W[off], acc);
+      acc = C::fmaj(U[off], W[off], acc);
     }
   }
   part[wid][lane] = acc;
   __syncthreads();
   if (wid != 0 || e >= d * d) return;
   acc = part[0][lane];
-  for (int w = 1; w < kPjWarps; ++w) acc = cadd(acc, part[w][lane]);
-  T.mats[pj.dst_mat][e] = acc;
+  for (int w = 1; w < kPjWarps; ++w) acc = C::add(acc, part[w][lane]);
+  ((V*)T.mats[pj.dst_mat])[e] = acc;
 }
 
-void launch_project(const DevTables& T, const PjList& L, cudaStream_t s) {
+void launch_project(int prec, const DevTables& T, const PjList& L, cudaStream_t s) {
   if (L.n_tiles <= 0) return;
-  k_project<<<L.n_tiles, 32 * kPjWarps, 0, s>>>(T, L);
+  if (prec == PREC_F32)
+    k_project<float><<<L.n_tiles, 32 * kPjWarps, 0, s>>>(T, L);
+  else
+    k_project<double><<<L.n_tiles, 32 * kPjWarps, 0, s>>>(T, L);
 }
 
 // ---------------------------------------------------------------------------
@@ -193,7 +245,8 @@ __device__ double block_sum(double v, double* red) {
 }
 
 __global__ void __launch_bounds__(kQrThreads) k_qr(double2* U, int d0, int d1, int d2, int leg,
-                                                   double tol, double2* A, double2* Q, double2* R, int* flag) {
+                                                   double tol, double2* A, double2* Q, double2* R, int* flag,
+                                                   float2* U_lo, float2* R_lo) {
   __shared__ double red[kQrThreads / 32];
   __shared__ double s_beta[kQrMaxN];
   __shared__ int s_skip[kQrMaxN];
@@ -277,6 +330,7 @@ __global__ void __launch_bounds__(kQrThreads) k_qr(double2* U, int d0, int d1, i
       v = make_double2(a.x * p.x + a.y * p.y, a.y * p.x - a.x * p.y);  // conj(p) * a
     }
     R[k] = v;
+    if (R_lo) R_lo[k] = make_float2((float)v.x, (float)v.y);
   }
   // Q = H_0 ... H_{n-1} [I; 0], column-major in Q
   for (int64_t k = tid; k < m * n; k += nt) {
@@ -305,24 +359,30 @@ __global__ void __launch_bounds__(kQrThreads) k_qr(double2* U, int d0, int d1, i
   for (int64_t k = tid; k < m * n; k += nt) {
     const int64_t c = k / m, r = k % m;
     const int64_t a = r / dd[lb], b = r % dd[lb];
-    U[c * st[leg] + a * st[la] + b * st[lb]] = cmul(Q[k], s_phase[c]);
+    const double2 q = cmul(Q[k], s_phase[c]);
+    const int64_t at = c * st[leg] + a * st[la] + b * st[lb];
+    U[at] = q;
+    if (U_lo) U_lo[at] = make_float2((float)q.x, (float)q.y);
   }
 }
 
 void launch_qr(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work,
-               double2* qbuf, double2* R, int* flag, cudaStream_t s) {
-  if (launch_qr_cluster(U, d0, d1, d2, leg, tol, R, flag, s)) return;
-  k_qr<<<1, kQrThreads, 0, s>>>(U, d0, d1, d2, leg, tol, work, qbuf, R, flag);
+               double2* qbuf, double2* R, int* flag, float2* U_lo, float2* R_lo, cudaStream_t s) {
+  if (launch_qr_cluster(U, d0, d1, d2, leg, tol, R, flag, U_lo, R_lo, s)) return;
+  k_qr<<<1, kQrThreads, 0, s>>>(U, d0, d1, d2, leg, tol, work, qbuf, R, flag, U_lo, R_lo);
 }
 
-__global__ void k_copy(double2* dst, const double2* src, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = src[i];
+__global__ void k_copy(double2* dst, float2* dst_lo, const double2* src, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = src[i];
+    dst[i] = v;
+    if (dst_lo) dst_lo[i] = make_float2((float)v.x, (float)v.y);
+  }
 }
-void launch_copy(double2* dst, const double2* src, int64_t n, cudaStream_t s) {
+void launch_copy(double2* dst, float2* dst_lo, const double2* src, int64_t n, cudaStream_t s) {
   if (n <= 0) return;
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
-  k_copy<<<blocks, 256, 0, s>>>(dst, src, n);
+  k_copy<<<blocks, 256, 0, s>>>(dst, dst_lo, src, n);
 }
 
 // ---------------------------------------------------------------------------
@@ -364,10 +424,11 @@ void launch_rdm_node(const double2* U, int d0, int d1, int d2, bool root, const 
   k_rdm_node<<<(nout + 127) / 128, 128, 0, s>>>(U, d0, d1, d2, root ? 1 : 0, w1, w2, out);
 }
 
-__global__ void k_drive(double2* const* mats, const DriveMat* list, int n, DriveArgs g) {
+__global__ void k_drive(double2* const* mats, float2* const* mats32, const DriveMat* list, int n, DriveArgs g) {
   const DriveMat dm = list[blockIdx.x];
   const int dd = dm.d * dm.d;
   double2* cur = mats[dm.cur];
+  float2* cur32 = mats32 ? mats32[dm.cur] : nullptr;
   const double2* st = mats[dm.stat];
   for (int e = threadIdx.x; e < dd; e += blockDim.x) {
     double2 v = st[e];
@@ -378,12 +439,13 @@ __global__ void k_drive(double2* const* mats, const DriveMat* list, int n, Drive
         v.y += g.g[d] * p.y;
       }
     cur[e] = v;
+    if (cur32) cur32[e] = make_float2((float)v.x, (float)v.y);
   }
 }
-void launch_drive(double2* const* mats_dev, const DriveMat* list, int n, const DriveArgs& g,
-                  cudaStream_t s) {
+void launch_drive(double2* const* mats_dev, float2* const* mats32, const DriveMat* list, int n,
+                  const DriveArgs& g, cudaStream_t s) {
   if (n <= 0) return;
-  k_drive<<<n, 128, 0, s>>>(mats_dev, list, n, g);
+  k_drive<<<n, 128, 0, s>>>(mats_dev, mats32, list, n, g);
 }
 
 __global__ void k_check_finite(const double2* x, int64_t n, int* flag) {

@@ -9,23 +9,33 @@
 
 namespace ttn {
 
-// Device-side view of the job tables (all pointers into the workspace).
+// Precision of the node/bond/environment contractions. The state (node
+// tensors, bond matrices), RK4 accumulation, QR, absorb and RDM are FP64 in
+// both modes; PREC_F32 runs the contractions in FP32 on FP32 shadow copies.
+enum Prec : int { PREC_F64 = 0, PREC_F32 = 1 };
+
+// Device-side view of the job tables. Element type of bufs/mats is the
+// contraction type of the table (double2 or float2).
 struct DevTables {
-  double2* const* bufs;   // buffer id -> tensor base
-  double2* const* mats;   // matrix id -> d x d matrix
+  void* const* bufs;   // buffer id -> tensor base
+  void* const* mats;   // matrix id -> d x d matrix
   const ApTerm* terms;
   const ApOut* outs;
   const PjOut* pjs;
 };
 
 // Epilogue of the apply kernel. STORE writes each output to its dst buffer;
-// RKs (s = 1..4) fuse the classical RK4 stage update of y with step h:
+// RKs (s = 1..4) fuse the classical RK4 stage update of the FP64 state y with
+// step h (k = the computed sum, acc and y in FP64, ys in the contraction type):
 //   s=1: acc = k;      ys = y + h/2 k      s=3: acc += 2k; ys = y + h k
-//   s=2: acc += 2k;    ys = y + h/2 k      s=4: y += h/6 (acc + k)
+//   s=2: acc += 2k;    ys = y + h/2 k      s=4: y += h/6 (acc + k), y_lo = y
 enum EpiMode : int { EPI_STORE = 0, EPI_RK1 = 1, EPI_RK2 = 2, EPI_RK3 = 3, EPI_RK4 = 4 };
 struct Epi {
   int mode;
-  int y, ys, acc;  // buffer ids
+  double2* y;    // FP64 state
+  void* y_lo;    // contraction-type copy of y refreshed at s = 4 (== y in FP64 mode)
+  void* ys;      // stage input (contraction type)
+  double2* acc;  // FP64 stage accumulator
   double h;
 };
 
@@ -33,33 +43,36 @@ struct Epi {
 constexpr int kMaxDrives = 8;
 struct DriveMat {
   int d;
-  int cur, stat;
-  int part[kMaxDrives];  // matrix ids, -1 if the drive has no part here
+  int cur, stat;         // ids in the FP64 matrix table
+  int part[kMaxDrives];  // FP64 matrix ids, -1 if the drive has no part here
 };
 struct DriveArgs {
   double g[kMaxDrives];
 };
 
-void launch_apply(const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s);
-void launch_project(const DevTables& T, const PjList& L, cudaStream_t s);
+void launch_apply(int prec, const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s);
+void launch_project(int prec, const DevTables& T, const PjList& L, cudaStream_t s);
 // Householder QR of node tensor U (dims d[3]) matricised toward leg `leg`.
 // U is overwritten with Q (same layout), R (d_leg x d_leg, row-major) written to R.
 // work: >= P complex, qbuf: >= P complex. A non-finite ||U||_F sets *flag and
-// leaves U unchanged.
+// leaves U unchanged. U_lo / R_lo (nullable) receive FP32 copies of Q and R.
 void launch_qr(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work,
-               double2* qbuf, double2* R, int* flag, cudaStream_t s);
+               double2* qbuf, double2* R, int* flag, float2* U_lo, float2* R_lo, cudaStream_t s);
 // Cluster-parallel variant (qr.cu); returns false when the shape does not fit
 // (bond dim > kQrClusterMaxN or the row blocks exceed shared memory).
 constexpr int kQrClusterMaxN = 64;
 bool launch_qr_cluster(double2* U, int d0, int d1, int d2, int leg, double tol, double2* R, int* flag,
-                       cudaStream_t s);
-void launch_copy(double2* dst, const double2* src, int64_t n, cudaStream_t s);
+                       float2* U_lo, float2* R_lo, cudaStream_t s);
+// dst = src (FP64); dst_lo (nullable) = FP32 copy.
+void launch_copy(double2* dst, float2* dst_lo, const double2* src, int64_t n, cudaStream_t s);
 // rho / vector contraction for one node: out[a] (non-root) or out[i*d1+j] (root)
 // = sum U[...] w1[.] w2[.] (w = nullptr means the n = 0 unit vector).
 void launch_rdm_node(const double2* U, int d0, int d1, int d2, bool root, const double2* w1,
                      const double2* w2, double2* out, cudaStream_t s);
-void launch_drive(double2* const* mats_dev, const DriveMat* list, int n, const DriveArgs& g,
-                  cudaStream_t s);
+// cur = stat + sum_d g_d part_d in the FP64 table; mats32 (nullable) receives
+// the FP32 copy of cur (same matrix id in the FP32 table).
+void launch_drive(double2* const* mats_dev, float2* const* mats32, const DriveMat* list, int n,
+                  const DriveArgs& g, cudaStream_t s);
 void launch_check_finite(const double2* x, int64_t n, int* flag, cudaStream_t s);
 
 }  // namespace ttn

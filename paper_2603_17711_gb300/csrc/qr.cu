@@ -73,7 +73,8 @@ __device__ double bsum(double v, double* red) {
 //   T   [n][n]   WY factor
 //   MM  [n][n]   T V_top^H
 __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int d1, int d2, int leg,
-                                                         double tol, double2* R, int* flag) {
+                                                         double tol, double2* R, int* flag, float2* U_lo,
+                                                         float2* R_lo) {
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int me = (int)cluster.block_rank();
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
       v = make_double2(a.x * p.x + a.y * p.y, a.y * p.x - a.x * p.y);  // conj(p) * a
     }
     R[k] = v;
+    if (R_lo) R_lo[k] = make_float2((float)v.x, (float)v.y);
   }
   // partial Gram G[a][b] = sum_{my rows} conj(v_a) v_b, v_a = 0 above the diagonal and for skipped a
   for (int k = tid; k < n * n; k += nt) {
@@ -297,8 +299,10 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
       q.y -= v.x * mm.y + v.y * mm.x;
     }
     const double2 p = s_phase[c];
-    U[c * st[leg] + (int64_t)(r / dd[lb]) * st[la] + (int64_t)(r % dd[lb]) * st[lb]] =
-        make_double2(q.x * p.x - q.y * p.y, q.x * p.y + q.y * p.x);
+    const double2 qp = make_double2(q.x * p.x - q.y * p.y, q.x * p.y + q.y * p.x);
+    const int64_t at = c * st[leg] + (int64_t)(r / dd[lb]) * st[la] + (int64_t)(r % dd[lb]) * st[lb];
+    U[at] = qp;
+    if (U_lo) U_lo[at] = make_float2((float)qp.x, (float)qp.y);
   }
   cluster.sync();  // keep shared memory alive until every remote read has finished
 }
@@ -310,7 +314,7 @@ size_t qr_cluster_smem(int m, int n, int C) {
 
 int qr_cluster_size(int m, int n) {
   if (n > kQrClusterMaxN) return 0;
-  int C = (m + 24) / 25;
+  int C = (m + 7) / 8;  // about 8 rows per CTA: the factorisation is FP64-issue bound
   C = C < 1 ? 1 : (C > 16 ? 16 : C);
   while (C > 1 && qr_cluster_smem(m, n, C) > 160 * 1024) --C;  // not expected for C <= 16
   if (qr_cluster_smem(m, n, C) > 160 * 1024) return 0;
@@ -318,7 +322,7 @@ int qr_cluster_size(int m, int n) {
 }
 
 bool launch_qr_cluster(double2* U, int d0, int d1, int d2, int leg, double tol, double2* R, int* flag,
-                       cudaStream_t s) {
+                       float2* U_lo, float2* R_lo, cudaStream_t s) {
   const int dd[3] = {d0, d1, d2};
   const int n = dd[leg];
   const int m = (int)((int64_t)d0 * d1 * d2 / n);
@@ -342,7 +346,7 @@ bool launch_qr_cluster(double2* U, int d0, int d1, int d2, int leg, double tol, 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_qr_cluster, U, d0, d1, d2, leg, tol, R, flag) == cudaSuccess;
+  return cudaLaunchKernelEx(&cfg, k_qr_cluster, U, d0, d1, d2, leg, tol, R, flag, U_lo, R_lo) == cudaSuccess;
 }
 
 }  // namespace ttn

@@ -188,3 +188,58 @@ def test_vmf_and_ps2_status(pkg):
         g.ttn_step(w.dt, pkg.TTN_VMF, 1)
     assert e.value.status == 7
     g.close()
+
+
+# ---------------------------------------------------------------------------
+# Mixed-precision form: node/bond/environment contractions in FP32 on FP32
+# shadows, state + RK4 accumulation + QR + absorb + RDM in FP64. Bar: RDM
+# max-abs <= 1e-6 against the FP64 oracle.
+# ---------------------------------------------------------------------------
+def gpu_mixed(pkg, w):
+    return pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0,
+                          drives=w.drives, precision=pkg.TTN_MIXED_FP32)
+
+
+def test_mixed_spin_boson_tt_1000_steps(pkg):
+    rows = np.loadtxt(os.path.join(HERE, "golden", "spin_boson_tt_k4_n10_r10.txt"))
+    steps = rows[:, 0].astype(int)
+    ref = (rows[:, 1::2] + 1j * rows[:, 2::2]).reshape(-1, 2, 2)
+    w = W.spin_boson_tt(n_steps=1000)
+    g = gpu_mixed(pkg, w)
+    err, n = 0.0, 0
+    for k, s in enumerate(steps):
+        if s > n:
+            g.ttn_step(w.dt, pkg.TTN_PS1, int(s - n))
+            n = int(s)
+        err = max(err, float(np.max(np.abs(g.ttn_rdm() - ref[k]))))
+    g.close()
+    assert err <= TOL_FP64
+
+
+@pytest.mark.parametrize("make", [lambda: W.exciton_chain(n_sites=3, rank=7, depth=4, n_steps=30),
+                                  lambda: W.exciton_chain(n_steps=2)])
+def test_mixed_exciton_chain(pkg, make):
+    w = make()
+    g = gpu_mixed(pkg, w)
+    o = ottn.from_workload(w)
+    err = 0.0
+    for _ in range(w.n_steps):
+        g.ttn_step(w.dt, pkg.TTN_PS1, 1)
+        o.step(w.dt, "ps1")
+        err = max(err, float(np.max(np.abs(g.ttn_rdm() - o.rdm()))))
+    g.close()
+    assert err <= TOL_FP64
+
+
+def test_mixed_driven_tls(pkg):
+    w = W.spin_boson_tt(depth=5, n_pade=2, rank=5, tree="btt")
+    w.drives = [W.Drive(V=W.SIGMA_X, amp=0.5, omega=3.0)]
+    g = gpu_mixed(pkg, w)
+    o = ottn.from_workload(w)
+    err = 0.0
+    for _ in range(40):
+        g.ttn_step(w.dt, pkg.TTN_PS1, 1)
+        o.step(w.dt, "ps1")
+        err = max(err, float(np.max(np.abs(g.ttn_rdm() - o.rdm()))))
+    g.close()
+    assert err <= TOL_FP64

@@ -6,7 +6,6 @@ from math import factorial
 import numpy as np
 import pytest
 from scipy import integrate
-import sympy
 
 from oracle import bcf
 
@@ -15,6 +14,7 @@ from oracle import bcf
 def test_pade_matches_bernoulli_taylor_series(N):
     # (f_BE(x) - 1/x - 1/2)/x = sum_n B_{2n+2}/(2n+2)! x^{2n}; the [N-1/N] Pade in x^2
     # reproduces the first 2N coefficients exactly.
+    sympy = pytest.importorskip("sympy")
     xi, eta = bcf.pade_bose_poles(N)
     B = [float(sympy.bernoulli(k)) for k in range(4 * N + 4)]
     for n in range(2 * N):
