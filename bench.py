@@ -234,6 +234,41 @@ def bench_ours(args, rank, world, local_rank):
     ga.close()
     gb.close()
 
+    # ---- batched: 256 uneven spin-boson instances in one graph launch per step ----
+    batch_out = None
+    if not args.no_batch:
+        bws = W.spin_boson_batch(n=args.batch)
+        hs = [make_gpu(pkg, bw, local_rank) for bw in bws]
+        pkg.ttn_batch_step(hs, 0.01, 1, args.warmup)
+        torch.cuda.synchronize()
+        s0 = hs[0].stream
+        ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(s0):
+            flush.zero_()
+        ta.record(s0)
+        pkg.ttn_batch_step(hs, 0.01, 1, args.steps)
+        tb.record(s0)
+        torch.cuda.synchronize()
+        ms_b = ta.elapsed_time(tb)
+        k1 = sum(hh.ttn_stats(0)[1] for hh in hs) / (args.warmup + args.steps)
+        # the same instances one after another (each its own step graph), few steps
+        n_seq = 2
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for hh in hs:
+            hh.ttn_step(0.01, 1, n_seq)
+        torch.cuda.synchronize()
+        seq_s = time.perf_counter() - t0
+        for hh in hs:
+            hh.close()
+        batch_out = {"workload": f"{args.batch} spin-boson instances (seeded lambda, omega_c, beta, eps, Delta; "
+                                 "K 2-8, depth 6-12, rank 8-32, BTT), ps1 FP64, dt 0.01",
+                     "instance_steps_per_s": args.batch * args.steps / (ms_b * 1e-3),
+                     "ms_per_batched_step": ms_b / args.steps,
+                     "sequential_instance_steps_per_s": args.batch * n_seq / seq_s,
+                     "node_contraction_gflop_per_batched_step": k1 / 1e9,
+                     "l2": "one 256 MB flush before the timed batch (the 256 states total ~0.3 GB)"}
+
     # ---- end to end through the public API with host buffers ----
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -287,6 +322,7 @@ def bench_ours(args, rank, world, local_rank):
         "e2e": {"value": world * args.steps / e2e_s, "unit": "steps/s",
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 16 * w.M * w.M,
                 "includes": "handle build, sop_load, workspace bind, rho0 upload, K steps with rho_S read back each step"},
+        "batched": batch_out,
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "wall_s_timed_region": wall,
@@ -334,6 +370,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch", type=int, default=256, help="instances in the batched leg")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -182,8 +182,14 @@ ttn_status ttn_time(ttn_t h, double* t);
 ttn_status ttn_substeps(ttn_t h, double tau, int32_t* m);
 
 /* Propagate several independent handles (same scheme and dt) in one call.
- * Every handle needs its own workspace and must not share a stream with
- * another handle in the list unless it is the same stream for all. */
+ * With ps1 and autonomous generators on non-default streams, every handle's
+ * captured step graph becomes one concurrent branch of a parent CUDA graph,
+ * launched n_steps times on the first handle's stream; the other handles'
+ * streams are ordered before and after the batch with events, so later calls
+ * on any member see the result. The parent graph is cached in the first handle
+ * and rebuilt when the member list, dt or a member's step graph changes.
+ * Otherwise (drives, default streams, profiling) the handles are stepped one
+ * after another. Every handle needs its own workspace. */
 ttn_status ttn_batch_step(ttn_t* hs, int32_t n, double dt, int32_t scheme, int32_t n_steps);
 
 /* Kernel accounting (instrumentation, not on the physics path). Kernel

@@ -18,7 +18,7 @@ from ._lib import (DRIVE_FN, TTN_FP64, TTN_MIXED_FP32, TTN_OK, TTN_PS1, TTN_PS2,
 from . import _lib
 
 __all__ = ["TTN", "TTNError", "heom", "TTN_FP64", "TTN_MIXED_FP32", "TTN_PS1", "TTN_PS2", "TTN_VMF",
-           "library", "from_model"]
+           "library", "from_model", "ttn_batch_step"]
 
 _LIB: Optional[C.CDLL] = None
 
@@ -186,6 +186,17 @@ class TTN:
         m = C.c_int32()
         self._check(self.lib.ttn_substeps(self.h, float(tau), C.byref(m)), "ttn_substeps")
         return int(m.value)
+
+
+def ttn_batch_step(handles: Sequence["TTN"], dt: float, scheme: int = TTN_PS1, n_steps: int = 1) -> None:
+    """Step several TTN handles together (C ABI ttn_batch_step)."""
+    if not handles:
+        return
+    arr = (C.c_void_p * len(handles))(*[t.h for t in handles])
+    st = library().ttn_batch_step(arr, len(handles), float(dt), int(scheme), int(n_steps))
+    if st != TTN_OK:
+        msg = library().ttn_last_error(handles[0].h)
+        raise TTNError(st, f"ttn_batch_step: {msg.decode() if msg else ''}")
 
 
 def from_model(H, baths, depth, parent, leg_node, ranks, rho0=None, drives=(), precision=TTN_FP64,

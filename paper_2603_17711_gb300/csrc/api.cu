@@ -74,16 +74,31 @@ struct ttn_ctx {
 
   // one ps1 step captured as a CUDA graph (autonomous generators, non-default stream)
   cudaGraphExec_t graph = nullptr;
+  cudaGraph_t graph_src = nullptr;  // kept for composition by ttn_batch_step
   double graph_dt = 0.0;
   bool graph_disabled = false;
   int64_t graph_launch[4] = {0, 0, 0, 0};
   double graph_flops[4] = {0, 0, 0, 0};
+  // batch graph owned by the first handle of the last ttn_batch_step call
+  cudaGraphExec_t batch_exec = nullptr;
+  std::vector<ttn_ctx*> batch_members;
+  std::vector<cudaGraphExec_t> batch_member_graphs;
+  double batch_dt = 0.0;
+  void drop_batch() {
+    if (batch_exec) cudaGraphExecDestroy(batch_exec);
+    batch_exec = nullptr;
+    batch_members.clear();
+    batch_member_graphs.clear();
+  }
   void drop_graph() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (graph_src) cudaGraphDestroy(graph_src);
     graph = nullptr;
+    graph_src = nullptr;
   }
 
   ~ttn_ctx() {
+    drop_batch();
     drop_graph();
     for (auto& m : marks) {
       cudaEventDestroy(m.a);
@@ -163,8 +178,8 @@ Layout layout_of(const Plan& p, int prec) {
   L.nodes = take(acc * sizeof(double2));
   L.pool = take(std::max<int64_t>(p.mat_pool, 1) * sizeof(double2));
   const int64_t r2 = (int64_t)p.r_max * p.r_max;
-  const int64_t nP = (int64_t)(3 + p.buf.n_t + p.buf.n_w) * p.P_max;
-  L.scratch_elems = nP + 3 * r2;
+  const int64_t nP = (int64_t)(4 + p.buf.n_t + p.buf.n_w) * p.P_max;
+  L.scratch_elems = nP + 4 * r2;
   L.scratch = take(L.scratch_elems * sizeof(double2));
   L.qr_elems = p.P_max;
   L.qr = take(L.qr_elems * sizeof(double2));
@@ -188,7 +203,7 @@ Layout layout_of(const Plan& p, int prec) {
     L.nodes32 = take(acc * sizeof(float2));
     L.pool32 = take(std::max<int64_t>(p.mat_pool, 1) * sizeof(float2));
     // ys, T_g, W_c and the bond shadow / stage input in FP32
-    L.scratch32 = take(((int64_t)(1 + p.buf.n_t + p.buf.n_w) * p.P_max + 2 * r2) * sizeof(float2));
+    L.scratch32 = take(((int64_t)(2 + p.buf.n_t + p.buf.n_w) * p.P_max + 3 * r2) * sizeof(float2));
     L.bufs_tab_lo = take(p.buf.n_bufs * sizeof(void*));
     L.mats_tab_lo = take(p.mats.size() * sizeof(void*));
   }
@@ -261,19 +276,24 @@ struct Exec {
     });
     run(3, 0.0, [&] { launch_copy(h->h_bufs[v], lo_copy(v), h->h_bufs[p.buf.tmp], p.P[v], s); });
   }
-  void rk4(const FlowLists& F, int y, int ys, int acc, double tau) {
+  // Stage inputs alternate between two buffers: stage 1 reads y and writes A,
+  // stage 2 reads A and writes B, stage 3 reads B and writes A, stage 4 reads A
+  // and updates y. A kernel never writes the buffer it reads.
+  void rk4(const FlowLists& F, int y, int ysA, int ysB, int acc, double tau) {
     const int m = p.n_sub(tau, h->params.kappa);
     const double hs = tau / m;
+    static const int src_var[5] = {0, 0, 1, 2, 1};
     for (int sub = 0; sub < m; ++sub)
       for (int st = 1; st <= 4; ++st) {
-        const int var = st == 1 ? 0 : 1;
+        const int var = src_var[st];
+        const int dst = st == 2 ? ysB : ysA;  // stage input written by this stage (unused at st = 4)
         store(0, F.first[var]);
-        apply(0, F.combine[var], Epi{st, h->h_bufs[y], h->h_bufs_lo[y], h->h_bufs_lo[ys], h->h_bufs[acc], hs});
+        apply(0, F.combine[var], Epi{st, h->h_bufs[y], h->h_bufs_lo[y], h->h_bufs_lo[dst], h->h_bufs[acc], hs});
       }
   }
-  void node_flow(int u, double tau) { rk4(p.node_flow[u], u, p.buf.ys, p.buf.acc, tau); }
+  void node_flow(int u, double tau) { rk4(p.node_flow[u], u, p.buf.ys, p.buf.ys2, p.buf.acc, tau); }
   void bond_flow(int a, int b, double tau) {
-    rk4(p.bond_flow[p.dir_id(a, b)], p.buf.bond_y, p.buf.bond_ys, p.buf.bond_acc, tau);
+    rk4(p.bond_flow[p.dir_id(a, b)], p.buf.bond_y, p.buf.bond_ys, p.buf.bond_ys2, p.buf.bond_acc, tau);
   }
 
   // Lie-Trotter half sweep Phi_h(u) and its adjoint (see oracle/ttn.py)
@@ -348,6 +368,46 @@ struct Exec {
     }
   }
 };
+
+
+// Capture one ps1 step of h as a CUDA graph (autonomous generator, non-default
+// stream, not profiling). Returns whether h->graph is usable for dt.
+bool ensure_graph(ttn_t h, double dt) {
+  const bool graphable = h->plan.n_drives == 0 && !h->profiling && h->stream != nullptr && !h->graph_disabled;
+  if (!graphable) return false;
+  if (h->graph && h->graph_dt == dt) return true;
+  h->drop_graph();
+  Exec ex(h);
+  int64_t l0[4];
+  double f0[4];
+  for (int c = 0; c < 4; ++c) {
+    l0[c] = h->n_launch[c];
+    f0[c] = h->n_flops[c];
+  }
+  cudaGraph_t g = nullptr;
+  bool ok = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    ex.step_ps1(dt, h->t);
+    ok = cudaStreamEndCapture(h->stream, &g) == cudaSuccess && g != nullptr;
+  }
+  if (ok) ok = cudaGraphInstantiate(&h->graph, g, 0) == cudaSuccess;
+  for (int c = 0; c < 4; ++c) {  // the captured launches did not run
+    h->graph_launch[c] = h->n_launch[c] - l0[c];
+    h->graph_flops[c] = h->n_flops[c] - f0[c];
+    h->n_launch[c] = l0[c];
+    h->n_flops[c] = f0[c];
+  }
+  if (!ok) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    h->drop_graph();
+    h->graph_disabled = true;
+    return false;
+  }
+  h->graph_src = g;
+  h->graph_dt = dt;
+  return true;
+}
 
 template <typename F>
 ttn_status guarded(ttn_t h, F&& f) {
@@ -510,7 +570,15 @@ ttn_status ttn_workspace_size(ttn_t h, size_t* bytes) {
 
 ttn_status ttn_set_stream(ttn_t h, void* stream) {
   if (!h) return TTN_EINVAL;
-  h->stream = (cudaStream_t)stream;
+  cudaStream_t ns = (cudaStream_t)stream;
+  if (h->ws_bound && ns != h->stream) {  // order the new stream after work queued on the old one
+    cudaEvent_t ev;
+    CUDA_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CUDA_TRY(h, cudaEventRecord(ev, h->stream));
+    CUDA_TRY(h, cudaStreamWaitEvent(ns, ev, 0));
+    cudaEventDestroy(ev);
+  }
+  h->stream = ns;
   h->drop_graph();
   return TTN_OK;
 }
@@ -539,6 +607,7 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
       return q;
     };
     h->h_bufs[p.buf.ys] = nxt(p.P_max);
+    h->h_bufs[p.buf.ys2] = nxt(p.P_max);
     h->h_bufs[p.buf.acc] = nxt(p.P_max);
     h->h_bufs[p.buf.tmp] = nxt(p.P_max);
     for (int i = 0; i < p.buf.n_t; ++i) h->h_bufs[p.buf.t0 + i] = nxt(p.P_max);
@@ -546,6 +615,7 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
     const int64_t r2 = (int64_t)p.r_max * p.r_max;
     h->h_bufs[p.buf.bond_y] = nxt(r2);
     h->h_bufs[p.buf.bond_ys] = nxt(r2);
+    h->h_bufs[p.buf.bond_ys2] = nxt(r2);
     h->h_bufs[p.buf.bond_acc] = nxt(r2);
     h->pool = (double2*)(base + L.pool);
     h->h_mats.assign(p.mats.size(), nullptr);
@@ -578,10 +648,12 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
         return (void*)q;
       };
       h->h_bufs_lo[p.buf.ys] = nx(p.P_max);
+      h->h_bufs_lo[p.buf.ys2] = nx(p.P_max);
       for (int i = 0; i < p.buf.n_t; ++i) h->h_bufs_lo[p.buf.t0 + i] = nx(p.P_max);
       for (int i = 0; i < p.buf.n_w; ++i) h->h_bufs_lo[p.buf.w0 + i] = nx(p.P_max);
       h->h_bufs_lo[p.buf.bond_y] = nx(r2);
       h->h_bufs_lo[p.buf.bond_ys] = nx(r2);
+      h->h_bufs_lo[p.buf.bond_ys2] = nx(r2);
       h->h_bufs_lo[p.buf.acc] = nullptr;       // accumulators stay FP64 (epilogue pointers)
       h->h_bufs_lo[p.buf.bond_acc] = nullptr;
       h->h_bufs_lo[p.buf.tmp] = nullptr;       // absorb runs in FP64
@@ -692,38 +764,7 @@ ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
     if (st != TTN_OK) return st;
     Exec ex(h);
     int k = 0;
-    const bool graphable = h->plan.n_drives == 0 && !h->profiling && h->stream != nullptr && !h->graph_disabled;
-    if (graphable && n_steps > 0 && (!h->graph || h->graph_dt != dt)) {
-      // capture one step; the launches recorded while capturing do not run
-      h->drop_graph();
-      int64_t l0[4];
-      double f0[4];
-      for (int c = 0; c < 4; ++c) {
-        l0[c] = h->n_launch[c];
-        f0[c] = h->n_flops[c];
-      }
-      cudaGraph_t g = nullptr;
-      bool ok = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-      if (ok) {
-        ex.step_ps1(dt, h->t);
-        ok = cudaStreamEndCapture(h->stream, &g) == cudaSuccess && g != nullptr;
-      }
-      if (ok) ok = cudaGraphInstantiate(&h->graph, g, 0) == cudaSuccess;
-      if (g) cudaGraphDestroy(g);
-      for (int c = 0; c < 4; ++c) {
-        h->graph_launch[c] = h->n_launch[c] - l0[c];
-        h->graph_flops[c] = h->n_flops[c] - f0[c];
-        h->n_launch[c] = l0[c];
-        h->n_flops[c] = f0[c];
-      }
-      if (!ok) {
-        cudaGetLastError();  // clear the capture error; run this call without a graph
-        h->drop_graph();
-        h->graph_disabled = true;
-      } else {
-        h->graph_dt = dt;
-      }
-    }
+    const bool graphable = ensure_graph(h, dt);
     if (graphable && h->graph) {
       for (; k < n_steps; ++k) {
         CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
@@ -828,11 +869,87 @@ ttn_status ttn_substeps(ttn_t h, double tau, int32_t* m) {
 
 ttn_status ttn_batch_step(ttn_t* hs, int32_t n, double dt, int32_t scheme, int32_t n_steps) {
   if (!hs || n < 0) return TTN_EINVAL;
-  for (int i = 0; i < n; ++i) {
-    ttn_status s = ttn_step(hs[i], dt, scheme, n_steps);
-    if (s != TTN_OK) return s;
-  }
-  return TTN_OK;
+  if (n == 0 || n_steps == 0) return TTN_OK;
+  for (int i = 0; i < n; ++i)
+    if (!hs[i]) return TTN_EINVAL;
+  ttn_t h0 = hs[0];
+  return guarded(h0, [&]() -> ttn_status {
+    if (!(std::isfinite(dt)) || dt <= 0 || n_steps < 0) return h0->fail(TTN_EINVAL, "bad dt or n_steps");
+    for (int i = 0; i < n; ++i) {
+      for (int j = 0; j < i; ++j)
+        if (hs[j] == hs[i]) return h0->fail(TTN_EINVAL, "a handle appears twice in the batch");
+      if (!hs[i]->ws_bound) return h0->fail(TTN_ESTATE, "a handle in the batch has no workspace");
+    }
+    // every member as one concurrent branch of a parent graph (ps1, autonomous)
+    bool all_graphs = scheme == TTN_PS1;
+    for (int i = 0; i < n && all_graphs; ++i) {
+      ttn_status st = ensure_envs(hs[i]);
+      if (st != TTN_OK) return h0->fail(st, std::string("batch member: ") + hs[i]->err);
+      if (hs[i]->plan.n_sub(dt, hs[i]->params.kappa) > (1 << 20)) return h0->fail(TTN_EINVAL, "dt too large");
+      all_graphs = ensure_graph(hs[i], dt);
+    }
+    if (!all_graphs) {  // drives, default streams or profiling: one handle after another
+      for (int i = 0; i < n; ++i) {
+        ttn_status st = ttn_step(hs[i], dt, scheme, n_steps);
+        if (st != TTN_OK) return h0->fail(st, std::string("batch member: ") + hs[i]->err);
+      }
+      return TTN_OK;
+    }
+    bool same = h0->batch_exec && h0->batch_dt == dt && (int)h0->batch_members.size() == n;
+    for (int i = 0; same && i < n; ++i)
+      same = h0->batch_members[i] == hs[i] && h0->batch_member_graphs[i] == hs[i]->graph;
+    if (!same) {
+      h0->drop_batch();
+      cudaGraph_t parent = nullptr;
+      CUDA_TRY(h0, cudaGraphCreate(&parent, 0));
+      for (int i = 0; i < n; ++i) {
+        cudaGraphNode_t node;
+        cudaError_t e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, hs[i]->graph_src);
+        if (e != cudaSuccess) {
+          cudaGraphDestroy(parent);
+          return cuda_fail(h0, e, "cudaGraphAddChildGraphNode");
+        }
+      }
+      cudaError_t e = cudaGraphInstantiate(&h0->batch_exec, parent, 0);
+      cudaGraphDestroy(parent);
+      if (e != cudaSuccess) return cuda_fail(h0, e, "cudaGraphInstantiate (batch)");
+      h0->batch_dt = dt;
+      for (int i = 0; i < n; ++i) {
+        h0->batch_members.push_back(hs[i]);
+        h0->batch_member_graphs.push_back(hs[i]->graph);
+      }
+    }
+    // order the batch after earlier work on every member stream, and later work after it
+    cudaStream_t s0 = h0->stream;
+    std::vector<cudaEvent_t> evs;
+    for (int i = 1; i < n; ++i)
+      if (hs[i]->stream != s0) {
+        cudaEvent_t ev;
+        CUDA_TRY(h0, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        evs.push_back(ev);
+        CUDA_TRY(h0, cudaEventRecord(ev, hs[i]->stream));
+        CUDA_TRY(h0, cudaStreamWaitEvent(s0, ev, 0));
+      }
+    for (int k = 0; k < n_steps; ++k) CUDA_TRY(h0, cudaGraphLaunch(h0->batch_exec, s0));
+    for (int i = 0; i < n; ++i) {
+      ttn_t h = hs[i];
+      for (int c = 0; c < 4; ++c) {
+        h->n_launch[c] += (int64_t)n_steps * h->graph_launch[c];
+        h->n_flops[c] += n_steps * h->graph_flops[c];
+      }
+      h->t += n_steps * dt;
+      launch_check_finite(h->h_bufs[0], h->plan.P[0], h->flag_dev, s0);
+    }
+    cudaEvent_t done;
+    CUDA_TRY(h0, cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    CUDA_TRY(h0, cudaEventRecord(done, s0));
+    for (int i = 1; i < n; ++i)
+      if (hs[i]->stream != s0) CUDA_TRY(h0, cudaStreamWaitEvent(hs[i]->stream, done, 0));
+    cudaEventDestroy(done);  // destruction is deferred until the event completes
+    for (auto ev : evs) cudaEventDestroy(ev);
+    CUDA_TRY(h0, cudaGetLastError());
+    return TTN_OK;
+  });
 }
 
 ttn_status ttn_stats(ttn_t h, int32_t kind, int64_t* launches, double* flops) {

@@ -519,12 +519,14 @@ std::string Plan::build_jobs() {
   pj_lists.clear();
   // buffer ids
   buf.ys = n;
-  buf.acc = n + 1;
-  buf.tmp = n + 2;
-  buf.bond_y = n + 3;
-  buf.bond_ys = n + 4;
-  buf.bond_acc = n + 5;
-  buf.t0 = n + 6;
+  buf.ys2 = n + 1;
+  buf.acc = n + 2;
+  buf.tmp = n + 3;
+  buf.bond_y = n + 4;
+  buf.bond_ys = n + 5;
+  buf.bond_ys2 = n + 6;
+  buf.bond_acc = n + 7;
+  buf.t0 = n + 8;
   // count pairs / classes to size T and W
   int max_pairs = 0, max_classes = 0;
   std::vector<ApTerm> singles;
@@ -569,8 +571,8 @@ std::string Plan::build_jobs() {
   // node flows
   node_flow.assign(n, {});
   for (int u = 0; u < n; ++u) {
-    for (int var = 0; var < 2; ++var) {
-      int src = var == 0 ? u : buf.ys;
+    for (int var = 0; var < 3; ++var) {
+      int src = var == 0 ? u : var == 1 ? buf.ys : buf.ys2;
       node_terms(u, src, 0, singles, pairs);
       ApOut base{dims[u][0], dims[u][1], dims[u][2], 0, 0, -1, 0, 0};
       if (!pairs.empty()) {
@@ -597,8 +599,8 @@ std::string Plan::build_jobs() {
       int a = dir ? p : c, b = dir ? c : p;
       int e = dir_id(a, b);
       int r = ranks[c];
-      for (int var = 0; var < 2; ++var) {
-        int src = var == 0 ? buf.bond_y : buf.bond_ys;
+      for (int var = 0; var < 3; ++var) {
+        int src = var == 0 ? buf.bond_y : var == 1 ? buf.bond_ys : buf.bond_ys2;
         bond_terms(a, b, src, singles, pairs);
         ApOut base{1, r, r, 0, 0, -1, 0, 0};
         if (!pairs.empty()) {

@@ -122,18 +122,21 @@ struct PjList {
 };
 
 // Buffer ids used by job lists. Node slots come first (0..n_nodes-1).
+// The RK4 stage input is double-buffered (ys, ys2): a combine kernel reads its
+// stage input along whole legs in other CTAs while its epilogue writes the next
+// stage input, so the two must never be the same buffer.
 struct BufIds {
-  int ys, acc, tmp;       // node-sized scratch
+  int ys, ys2, acc, tmp;  // node-sized scratch
   int t0, n_t;            // pair intermediates T_0..T_{n_t-1}
   int w0, n_w;            // env class outputs W_0..W_{n_w-1}
-  int bond_y, bond_ys, bond_acc;  // bond matrices as (1, d, d) tensors
+  int bond_y, bond_ys, bond_ys2, bond_acc;  // bond matrices as (1, d, d) tensors
   int n_bufs;
 };
 
-// Job lists of one node flow / bond flow (two source variants: state / stage input).
+// Job lists of one node flow / bond flow, per source: 0 = the state, 1 = ys, 2 = ys2.
 struct FlowLists {
-  int first[2] = {-1, -1};    // ApList ids (pairs' first mode products), -1 if no pairs
-  int combine[2] = {-1, -1};  // ApList ids (sum with RK4 epilogue)
+  int first[3] = {-1, -1, -1};    // ApList ids (pairs' first mode products), -1 if no pairs
+  int combine[3] = {-1, -1, -1};  // ApList ids (sum with RK4 epilogue)
 };
 struct EnvLists {
   int first = -1;    // ApList id

@@ -159,6 +159,21 @@ def test_exciton_chain_full_size_first_steps(pkg):
     assert err <= TOL_SHORT
 
 
+def test_concurrent_handles_match_oracle(pkg):
+    """Handles on their own streams run concurrently; each must still match the
+    oracle (guards against cross-CTA read/write hazards that only show under load)."""
+    ws = W.spin_boson_batch(n=6, n_steps=6)
+    gs = [gpu_from(pkg, w) for w in ws]
+    for g, w in zip(gs, ws):
+        g.ttn_step(w.dt, pkg.TTN_PS1, 6)
+    for g, w in zip(gs, ws):
+        o = ottn.from_workload(w)
+        for _ in range(6):
+            o.step(w.dt, "ps1")
+        assert np.max(np.abs(g.ttn_rdm() - o.rdm())) <= TOL_SHORT
+        g.close()
+
+
 def test_bitwise_deterministic(pkg):
     w = W.spin_boson_tt(depth=6, n_pade=3, rank=6, tree="btt")
     outs = []
@@ -243,3 +258,32 @@ def test_mixed_driven_tls(pkg):
         err = max(err, float(np.max(np.abs(g.ttn_rdm() - o.rdm()))))
     g.close()
     assert err <= TOL_FP64
+
+
+def test_batched_instances_equal_individual_runs(pkg):
+    """Uneven spin-boson instances (K, depth, rank, parameters all different)
+    stepped together by ttn_batch_step give bitwise the results of stepping
+    each alone, and agree with the oracle."""
+    ws = W.spin_boson_batch(n=6, n_steps=6)
+    batch = [gpu_from(pkg, w) for w in ws]
+    alone = [gpu_from(pkg, w) for w in ws]
+    pkg.ttn_batch_step(batch, 0.01, pkg.TTN_PS1, 6)
+    for g, w in zip(alone, ws):
+        g.ttn_step(w.dt, pkg.TTN_PS1, 6)
+    for gb, ga, w in zip(batch, alone, ws):
+        rb, ra = gb.ttn_rdm(), ga.ttn_rdm()
+        assert np.array_equal(rb, ra)
+        assert abs(gb.ttn_time() - 0.06) < 1e-12
+    for gb, w in zip(batch, ws):
+        o = ottn.from_workload(w)
+        for _ in range(6):
+            o.step(0.01, "ps1")
+        assert np.max(np.abs(gb.ttn_rdm() - o.rdm())) <= TOL_SHORT
+    # a second call reuses the cached parent graph
+    pkg.ttn_batch_step(batch, 0.01, pkg.TTN_PS1, 2)
+    for g in alone:
+        g.ttn_step(0.01, pkg.TTN_PS1, 2)
+    for gb, ga in zip(batch, alone):
+        assert np.array_equal(gb.ttn_rdm(), ga.ttn_rdm())
+    for g in batch + alone:
+        g.close()
