@@ -51,6 +51,13 @@ struct ttn_ctx {
   double2* pool = nullptr;
   int prec = PREC_F64;
   double2* qr_work = nullptr;
+  // ps2 scratch
+  double2 *svd_A = nullptr, *svd_V = nullptr, *svd_Z = nullptr, *svd_Zg = nullptr, *svd_C = nullptr;
+  double* svd_sigma = nullptr;
+  int* svd_perm = nullptr;
+  int* svd_info = nullptr;
+  std::vector<double> discarded;  // discarded weight of every ps2 split (host log)
+  std::vector<int> init_ranks;
   double2* rdm_vec = nullptr;
   double2* rho_dev = nullptr;
   int* flag_dev = nullptr;
@@ -155,6 +162,7 @@ ttn_status cuda_fail(ttn_t h, cudaError_t e, const char* what) {
 struct Layout {
   size_t nodes, pool, scratch, qr, rdm, rho, bufs_tab, mats_tab, terms, outs, pjs, drives, flag, total;
   size_t nodes32 = 0, pool32 = 0, scratch32 = 0, bufs_tab_lo = 0, mats_tab_lo = 0;  // FP32 mode only
+  size_t svd_small = 0;
   std::vector<int64_t> node_off;  // complex elements from `nodes`
   std::vector<int64_t> rdm_off;
   int64_t scratch_elems = 0, qr_elems = 0, rdm_elems = 0;
@@ -173,21 +181,22 @@ Layout layout_of(const Plan& p, int prec) {
   int64_t acc = 0;
   for (int u = 0; u < n; ++u) {
     L.node_off[u] = acc;
-    acc += (p.P[u] + 15) / 16 * 16;
+    acc += (p.P_cap[u] + 15) / 16 * 16;
   }
+  const int64_t S = std::max(p.P_cap_max, p.theta_cap);  // node-sized scratch capacity
   L.nodes = take(acc * sizeof(double2));
   L.pool = take(std::max<int64_t>(p.mat_pool, 1) * sizeof(double2));
-  const int64_t r2 = (int64_t)p.r_max * p.r_max;
-  const int64_t nP = (int64_t)(4 + p.buf.n_t + p.buf.n_w) * p.P_max;
-  L.scratch_elems = nP + 4 * r2;
+  const int64_t r2 = (int64_t)p.r_cap_max * p.r_cap_max;
+  const int64_t nP = (int64_t)(4 + p.buf.n_t + p.buf.n_w) * S;
+  L.scratch_elems = nP + 4 * r2 + 4 * p.theta_cap + 5 * p.theta_cap;
   L.scratch = take(L.scratch_elems * sizeof(double2));
-  L.qr_elems = p.P_max;
+  L.qr_elems = S;
   L.qr = take(L.qr_elems * sizeof(double2));
   L.rdm_off.resize(n);
   int64_t ra = 0;
   for (int u = 0; u < n; ++u) {
     L.rdm_off[u] = ra;
-    ra += p.dims[u][0];
+    ra += p.cap_dims[u][0];
   }
   L.rdm_elems = ra;
   L.rdm = take(ra * sizeof(double2));
@@ -198,12 +207,13 @@ Layout layout_of(const Plan& p, int prec) {
   L.outs = take(p.ap_outs.size() * sizeof(ApOut));
   L.pjs = take(p.pj_outs.size() * sizeof(PjOut));
   L.drives = take(p.locals.size() * sizeof(DriveMat));
+  L.svd_small = take(p.theta_cap * sizeof(double) + (p.theta_cap + 4) * sizeof(int));
   L.flag = take(sizeof(int) * 4);
   if (prec == PREC_F32) {
     L.nodes32 = take(acc * sizeof(float2));
     L.pool32 = take(std::max<int64_t>(p.mat_pool, 1) * sizeof(float2));
     // ys, T_g, W_c and the bond shadow / stage input in FP32
-    L.scratch32 = take(((int64_t)(2 + p.buf.n_t + p.buf.n_w) * p.P_max + 3 * r2) * sizeof(float2));
+    L.scratch32 = take(((int64_t)(2 + p.buf.n_t + p.buf.n_w) * S + 3 * r2 + 3 * p.theta_cap) * sizeof(float2));
     L.bufs_tab_lo = take(p.buf.n_bufs * sizeof(void*));
     L.mats_tab_lo = take(p.mats.size() * sizeof(void*));
   }
@@ -348,6 +358,122 @@ struct Exec {
       phi_adj(0, hh, true);
     }
   }
+  // ---- ps2 (adaptive rank): see oracle/ttn.py psi / psi_adj / two_site ----
+  cudaError_t err = cudaSuccess;
+  void note(cudaError_t e) {
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+  }
+  // new dims -> job lists rebuilt on the host and re-uploaded (queued kernels
+  // still read the old tables, so the stream is drained first)
+  void upload_jobs() {
+    note(cudaStreamSynchronize(s));
+    note(cudaMemcpy((void*)h->T.terms, p.ap_terms.data(), p.ap_terms.size() * sizeof(ApTerm), cudaMemcpyHostToDevice));
+    note(cudaMemcpy((void*)h->T.outs, p.ap_outs.data(), p.ap_outs.size() * sizeof(ApOut), cudaMemcpyHostToDevice));
+    if (!p.pj_outs.empty())
+      note(cudaMemcpy((void*)h->T.pjs, p.pj_outs.data(), p.pj_outs.size() * sizeof(PjOut), cudaMemcpyHostToDevice));
+    h->drop_graph();
+  }
+  void set_rank(int child, int r) {
+    if (p.ranks[child] == r) return;
+    p.ranks[child] = r;
+    p.update_dims();
+    p.build_jobs();
+    upload_jobs();
+  }
+  void two_site(int first, int second, double hh, int centre_to) {
+    if (err != cudaSuccess) return;
+    const int lf = p.tree.leg_index(first, second), ls = p.tree.leg_index(second, first);
+    const int fd[3] = {p.dims[first][0], p.dims[first][1], p.dims[first][2]};
+    const int sd[3] = {p.dims[second][0], p.dims[second][1], p.dims[second][2]};
+    const std::array<int, 4> td = p.theta_dims(first, second);
+    const int m = td[0] * td[1], n = td[2] * td[3];
+    const int tl = p.buf.th_y;
+    run(3, 0.0, [&] {
+      launch_merge(h->h_bufs[first], fd, lf, h->h_bufs[second], sd, ls, h->h_bufs[tl], lo_copy(tl), s);
+    });
+    rk4(p.two_site[p.dir_id(first, second)], tl, p.buf.th_ys, p.buf.th_ys2, p.buf.th_acc, hh);
+    const int nc = std::min(m, n), nr = std::max(m, n);
+    run(2, 0.0, [&] {
+      launch_jacobi_svd(h->h_bufs[tl], m, n, h->svd_A, h->svd_V, h->svd_sigma, h->svd_info, s);
+    });
+    std::vector<double> sig(nc);
+    int info[2] = {0, 0};
+    note(cudaMemcpyAsync(sig.data(), h->svd_sigma, nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+    note(cudaMemcpyAsync(info, h->svd_info, sizeof(info), cudaMemcpyDeviceToHost, s));
+    note(cudaStreamSynchronize(s));
+    if (err != cudaSuccess) return;
+    h->n_flops[2] += 8.0 * 4.0 * info[0] * 0.5 * nc * (nc - 1) * (double)(nr + nc);
+    // truncation (host): r0 = #{sigma > ps2_atol}, r = min(cap, max(1, ceil(ratio r0)))
+    std::vector<int> perm(nc);
+    for (int i = 0; i < nc; ++i) perm[i] = i;
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return sig[a] > sig[b]; });
+    int r0 = 0;
+    for (int i = 0; i < nc; ++i) r0 += sig[i] > h->params.ps2_atol ? 1 : 0;
+    const int cap = std::min(h->params.max_rank, nc);
+    const int r = std::min(cap, std::max(1, (int)std::ceil(h->params.ps2_ratio * r0 - 1e-9)));
+    const double smax = sig[perm[0]];
+    int g = 0;
+    while (g < r && smax > 0 && sig[perm[g]] > h->params.svd_tol * smax) ++g;
+    double disc = 0.0;
+    for (int i = r; i < nc; ++i) disc += sig[perm[i]] * sig[perm[i]];
+    h->discarded.push_back(std::sqrt(disc));
+    note(cudaMemcpy(h->svd_perm, perm.data(), r * sizeof(int), cudaMemcpyHostToDevice));
+    const bool iso_first = centre_to == second;
+    const int rows_iso = iso_first ? m : n;
+    run(3, 0.0, [&] {
+      launch_svd_vecs(h->svd_A, h->svd_V, h->svd_sigma, m, n, h->svd_perm, r, g, iso_first, h->svd_Z, h->svd_Zg,
+                      h->svd_C, s);
+    });
+    if (g < r) {  // deterministic completion of the undetermined directions (Householder, tol 0)
+      run(2, 0.0, [&] {
+        launch_qr(h->svd_Z, rows_iso, 1, r, 2, 0.0, h->qr_work, h->h_bufs[p.buf.tmp], h->svd_V, h->flag_dev,
+                  nullptr, nullptr, s);
+      });
+      run(3, 0.0, [&] { launch_restore_cols(h->svd_Z, h->svd_Zg, rows_iso, r, g, s); });
+    }
+    const int child = p.tree.parent[first] == second ? first : second;
+    set_rank(child, r);
+    const int nfd[3] = {p.dims[first][0], p.dims[first][1], p.dims[first][2]};
+    const int nsd[3] = {p.dims[second][0], p.dims[second][1], p.dims[second][2]};
+    run(3, 0.0, [&] {
+      launch_write_pair(h->h_bufs[first], lo_copy(first), nfd, lf, h->h_bufs[second], lo_copy(second), nsd, ls,
+                        h->svd_Z, h->svd_C, r, iso_first, s);
+    });
+  }
+  void psi(int u, double hh, bool last) {
+    const auto& ch = p.tree.children[u];
+    for (size_t idx = 0; idx < ch.size(); ++idx) {
+      const int c = ch[idx];
+      qr(u, c);
+      absorb(c, u);
+      env(u, c);
+      psi(c, hh, false);
+      two_site(c, u, hh, u);
+      env(c, u);
+      if (!(last && idx + 1 == ch.size())) node_flow(u, -hh);
+    }
+  }
+  void psi_adj(int u, double hh, bool first_call) {
+    const auto& ch = p.tree.children[u];
+    for (size_t k = 0; k < ch.size(); ++k) {
+      const int c = ch[ch.size() - 1 - k];
+      if (!(first_call && k == 0)) node_flow(u, -hh);
+      two_site(u, c, hh, c);
+      env(u, c);
+      psi_adj(c, hh, false);
+      qr(c, u);
+      env(c, u);
+      absorb(u, c);
+    }
+  }
+  void step_ps2(double dt, double t0) {
+    const double hh = 0.5 * dt;
+    drive(t0 + 0.25 * dt);
+    psi(0, hh, true);
+    drive(t0 + 0.75 * dt);
+    psi_adj(0, hh, true);
+  }
+
   void rebuild_envs() {
     drive(h->t);
     for (int c : p.tree.postorder)
@@ -442,6 +568,14 @@ ttn_status upload_pair(ttn_t h, double2* dst, void* dst_lo, const double2* src, 
 
 ttn_status upload_initial(ttn_t h, const double* rho0) {
   Plan& p = h->plan;
+  if (!h->init_ranks.empty() && p.ranks != h->init_ranks) {  // ps2 changed them
+    Exec ex(h);
+    p.ranks = h->init_ranks;
+    p.update_dims();
+    p.build_jobs();
+    ex.upload_jobs();
+    if (ex.err != cudaSuccess) return cuda_fail(h, ex.err, "job upload");
+  }
   const int M = p.leg_dims[0];
   cudaStream_t s = h->stream;
   for (int u = 0; u < p.tree.n_nodes; ++u) {
@@ -511,6 +645,14 @@ ttn_status ttn_set_params(ttn_t h, const ttn_params* prm) {
       return h->fail(TTN_EINVAL, "parameter out of range");
     if (h->ws_bound && prm->max_rank != h->params.max_rank)
       return h->fail(TTN_ESTATE, "max_rank must be set before the workspace is bound");
+    if (prm->max_rank != h->plan.cap_rank) {
+      h->plan.set_caps(prm->max_rank);
+      if (h->plan.r_cap_max > 256) return h->fail(TTN_EUNSUPPORTED, "bond ranks above 256");
+      if (h->sop_loaded) {
+        std::string e = h->plan.rebuild_classes();
+        if (!e.empty()) return h->fail(TTN_EINVAL, e);
+      }
+    }
     h->params = *prm;
     h->drop_graph();  // substep counts and tolerances are baked into a captured step
     return TTN_OK;
@@ -606,13 +748,26 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
       o += n;
       return q;
     };
-    h->h_bufs[p.buf.ys] = nxt(p.P_max);
-    h->h_bufs[p.buf.ys2] = nxt(p.P_max);
-    h->h_bufs[p.buf.acc] = nxt(p.P_max);
-    h->h_bufs[p.buf.tmp] = nxt(p.P_max);
-    for (int i = 0; i < p.buf.n_t; ++i) h->h_bufs[p.buf.t0 + i] = nxt(p.P_max);
-    for (int i = 0; i < p.buf.n_w; ++i) h->h_bufs[p.buf.w0 + i] = nxt(p.P_max);
-    const int64_t r2 = (int64_t)p.r_max * p.r_max;
+    const int64_t S = std::max(p.P_cap_max, p.theta_cap);
+    h->h_bufs[p.buf.ys] = nxt(S);
+    h->h_bufs[p.buf.ys2] = nxt(S);
+    h->h_bufs[p.buf.acc] = nxt(S);
+    h->h_bufs[p.buf.tmp] = nxt(S);
+    for (int i = 0; i < p.buf.n_t; ++i) h->h_bufs[p.buf.t0 + i] = nxt(S);
+    for (int i = 0; i < p.buf.n_w; ++i) h->h_bufs[p.buf.w0 + i] = nxt(S);
+    h->h_bufs[p.buf.th_y] = nxt(p.theta_cap);
+    h->h_bufs[p.buf.th_ys] = nxt(p.theta_cap);
+    h->h_bufs[p.buf.th_ys2] = nxt(p.theta_cap);
+    h->h_bufs[p.buf.th_acc] = nxt(p.theta_cap);
+    h->svd_A = nxt(p.theta_cap);
+    h->svd_V = nxt(p.theta_cap);
+    h->svd_Z = nxt(p.theta_cap);
+    h->svd_Zg = nxt(p.theta_cap);
+    h->svd_C = nxt(p.theta_cap);
+    h->svd_sigma = (double*)(base + L.svd_small);
+    h->svd_perm = (int*)(h->svd_sigma + p.theta_cap);
+    h->svd_info = h->svd_perm + p.theta_cap;
+    const int64_t r2 = (int64_t)p.r_cap_max * p.r_cap_max;
     h->h_bufs[p.buf.bond_y] = nxt(r2);
     h->h_bufs[p.buf.bond_ys] = nxt(r2);
     h->h_bufs[p.buf.bond_ys2] = nxt(r2);
@@ -647,10 +802,14 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
         o32 += n;
         return (void*)q;
       };
-      h->h_bufs_lo[p.buf.ys] = nx(p.P_max);
-      h->h_bufs_lo[p.buf.ys2] = nx(p.P_max);
-      for (int i = 0; i < p.buf.n_t; ++i) h->h_bufs_lo[p.buf.t0 + i] = nx(p.P_max);
-      for (int i = 0; i < p.buf.n_w; ++i) h->h_bufs_lo[p.buf.w0 + i] = nx(p.P_max);
+      h->h_bufs_lo[p.buf.ys] = nx(S);
+      h->h_bufs_lo[p.buf.ys2] = nx(S);
+      for (int i = 0; i < p.buf.n_t; ++i) h->h_bufs_lo[p.buf.t0 + i] = nx(S);
+      for (int i = 0; i < p.buf.n_w; ++i) h->h_bufs_lo[p.buf.w0 + i] = nx(S);
+      h->h_bufs_lo[p.buf.th_y] = nx(p.theta_cap);
+      h->h_bufs_lo[p.buf.th_ys] = nx(p.theta_cap);
+      h->h_bufs_lo[p.buf.th_ys2] = nx(p.theta_cap);
+      h->h_bufs_lo[p.buf.th_acc] = nullptr;
       h->h_bufs_lo[p.buf.bond_y] = nx(r2);
       h->h_bufs_lo[p.buf.bond_ys] = nx(r2);
       h->h_bufs_lo[p.buf.bond_ys2] = nx(r2);
@@ -726,6 +885,7 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
     CUDA_TRY(h, cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
     h->ws_bound = true;
+    h->init_ranks = p.ranks;
     const int M = p.leg_dims[0];
     std::vector<double> rho0(2 * M * M, 0.0);
     rho0[0] = 1.0;
@@ -754,9 +914,19 @@ ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
     if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
     if (!(std::isfinite(dt)) || dt <= 0 || n_steps < 0) return h->fail(TTN_EINVAL, "bad dt or n_steps");
     if (scheme == TTN_VMF) return h->fail(TTN_EUNSUPPORTED, "vmf is not implemented");
-    if (scheme != TTN_PS1) {
-      if (scheme == TTN_PS2) return h->fail(TTN_EUNSUPPORTED, "ps2 is not implemented on the GPU yet");
-      return h->fail(TTN_EINVAL, "unknown scheme");
+    if (scheme != TTN_PS1 && scheme != TTN_PS2) return h->fail(TTN_EINVAL, "unknown scheme");
+    if (scheme == TTN_PS2) {
+      ttn_status st = ensure_envs(h);
+      if (st != TTN_OK) return st;
+      Exec ex(h);
+      for (int k = 0; k < n_steps; ++k) {
+        ex.step_ps2(dt, h->t);
+        if (ex.err != cudaSuccess) return cuda_fail(h, ex.err, "ps2 step");
+        h->t += dt;
+      }
+      ex.run(3, 0.0, [&] { launch_check_finite(h->h_bufs[0], h->plan.P[0], h->flag_dev, h->stream); });
+      CUDA_TRY(h, cudaGetLastError());
+      return TTN_OK;
     }
     if (h->plan.n_sub(dt, h->params.kappa) > (1 << 20))
       return h->fail(TTN_EINVAL, "dt * Lambda needs more than 2^20 RK4 substeps");

@@ -72,9 +72,17 @@ template <> struct Cx<float> {
 // ---------------------------------------------------------------------------
 constexpr int kApWarps = 8;
 
+// Leg geometry of one output element (kept in registers: selected by switch,
+// never indexed dynamically).
+struct Geo {
+  int d0, d1, d2, d3;
+  int i0, i1, i2, i3;
+  int64_t s0, s1, s2;  // s3 = 1
+};
+
 template <typename R>
 __device__ __forceinline__ typename Cx<R>::T term_dot(const ApTerm& term, const DevTables& T, int64_t idx,
-                                                      int i0, int i1, int i2, int d0, int d1, int d2) {
+                                                      const Geo& g) {
   using C = Cx<R>;
   using V = typename C::T;
   const V* __restrict__ src = (const V*)T.bufs[term.src];
@@ -82,12 +90,11 @@ __device__ __forceinline__ typename Cx<R>::T term_dot(const ApTerm& term, const 
   const V* __restrict__ M = (const V*)T.mats[term.mat];
   int dl, il;
   int64_t stride;
-  if (term.leg == 0) {
-    dl = d0; il = i0; stride = (int64_t)d1 * d2;
-  } else if (term.leg == 1) {
-    dl = d1; il = i1; stride = d2;
-  } else {
-    dl = d2; il = i2; stride = 1;
+  switch (term.leg) {
+    case 0: dl = g.d0; il = g.i0; stride = g.s0; break;
+    case 1: dl = g.d1; il = g.i1; stride = g.s1; break;
+    case 2: dl = g.d2; il = g.i2; stride = g.s2; break;
+    default: dl = g.d3; il = g.i3; stride = 1; break;
   }
   const V* __restrict__ row = M + (int64_t)il * dl;
   const V* __restrict__ col = src + (idx - (int64_t)il * stride);
@@ -106,16 +113,21 @@ __global__ void __launch_bounds__(32 * kApWarps) k_apply(DevTables T, ApList L, 
   int o = L.out_begin;
   while (o + 1 < L.out_end && T.outs[o + 1].tile0 <= tile) ++o;
   const ApOut out = T.outs[o];
-  const int d0 = out.d0, d1 = out.d1, d2 = out.d2;
-  const int64_t P = (int64_t)d0 * d1 * d2;
+  Geo g;
+  g.d0 = out.d0; g.d1 = out.d1; g.d2 = out.d2; g.d3 = out.d3;
+  g.s2 = g.d3;
+  g.s1 = (int64_t)g.d2 * g.d3;
+  g.s0 = g.s1 * g.d1;
+  const int64_t P = g.s0 * g.d0;
   const int64_t idx = (int64_t)(tile - out.tile0) * kApTile + lane;
   V acc = C::zero();
   if (idx < P) {
-    const int i2 = (int)(idx % d2);
-    const int i1 = (int)((idx / d2) % d1);
-    const int i0 = (int)(idx / ((int64_t)d1 * d2));
+    g.i0 = (int)(idx / g.s0);
+    g.i1 = (int)((idx / g.s1) % g.d1);
+    g.i2 = (int)((idx / g.s2) % g.d2);
+    g.i3 = (int)(idx % g.d3);
     for (int t = out.term_begin + wid; t < out.term_end; t += kApWarps)
-      acc = C::add(acc, term_dot<R>(T.terms[t], T, idx, i0, i1, i2, d0, d1, d2));
+      acc = C::add(acc, term_dot<R>(T.terms[t], T, idx, g));
   }
   part[wid][lane] = acc;
   __syncthreads();

@@ -75,4 +75,18 @@ void launch_drive(double2* const* mats_dev, float2* const* mats32, const DriveMa
                   const DriveArgs& g, cudaStream_t s);
 void launch_check_finite(const double2* x, int64_t n, int* flag, cudaStream_t s);
 
+// ps2 two-site kernels (ps2.cu), FP64. fd/sd: dims of the first/second node,
+// lf/ls: the leg of each facing the other.
+void launch_merge(const double2* Uf, const int* fd, int lf, const double2* Us, const int* sd, int ls,
+                  double2* theta, float2* theta_lo, cudaStream_t s);
+// One-sided Jacobi SVD of theta (m x n row-major). A: >= m*n, V: >= min(m,n)^2,
+// sigma: min(m,n) (unsorted), info[0] = sweeps, info[1] = 1 if Theta^H was used.
+void launch_jacobi_svd(const double2* theta, int m, int n, double2* A, double2* V, double* sigma, int* info,
+                       cudaStream_t s);
+void launch_svd_vecs(const double2* A, const double2* V, const double* sigma, int m, int n, const int* perm, int r,
+                     int g, bool iso_first, double2* Z, double2* Zg, double2* Cm, cudaStream_t s);
+void launch_restore_cols(double2* Z, const double2* Zg, int rows, int r, int g, cudaStream_t s);
+void launch_write_pair(double2* Uf, float2* Uf_lo, const int* fd, int lf, double2* Us, float2* Us_lo, const int* sd,
+                       int ls, const double2* Z, const double2* Cm, int r, bool iso_first, cudaStream_t s);
+
 }  // namespace ttn

@@ -192,15 +192,24 @@ std::string Plan::build(int n_nodes, const int32_t* parent, int n_legs, const in
   for (int l = 0; l < n_legs; ++l)
     if (leg_dims[l] < 1) return "leg dimension < 1";
   if (leg_dims[0] != leg_dims[1]) return "legs 0 and 1 (system ket/bra) must have equal dimension";
-  std::vector<int> req(rk, rk + n_nodes);
+  req.assign(rk, rk + n_nodes);
+  req[0] = 0;
   for (int u = 1; u < n_nodes; ++u)
     if (req[u] < 1) return "rank < 1";
   ranks = effective_ranks(tree, leg_dims, req);
-  dims.assign(n_nodes, {0, 0, 0});
-  P.assign(n_nodes, 0);
+  update_dims();
+  set_caps(cap_rank);
+  if (r_cap_max > 256) return "UNSUPPORTED: bond ranks above 256 (QR kernel limit)";
+  return "";
+}
+
+void Plan::update_dims() {
+  const int n = tree.n_nodes;
+  dims.assign(n, {0, 0, 0});
+  P.assign(n, 0);
   P_max = 0;
   r_max = 1;
-  for (int u = 0; u < n_nodes; ++u) {
+  for (int u = 0; u < n; ++u) {
     int64_t p = 1;
     for (int i = 0; i < 3; ++i) {
       const Leg& L = tree.legs[u][i];
@@ -211,9 +220,37 @@ std::string Plan::build(int n_nodes, const int32_t* parent, int n_legs, const in
     P[u] = p;
     P_max = std::max(P_max, p);
   }
-  for (int u = 1; u < n_nodes; ++u) r_max = std::max(r_max, ranks[u]);
-  if (r_max > 256) return "UNSUPPORTED: bond ranks above 256 (QR kernel limit)";
-  return "";
+  for (int u = 1; u < n; ++u) r_max = std::max(r_max, ranks[u]);
+}
+
+void Plan::set_caps(int max_rank) {
+  const int n = tree.n_nodes;
+  cap_rank = max_rank;
+  std::vector<int> want(n, 0);
+  for (int u = 1; u < n; ++u) want[u] = std::max(req[u], max_rank);
+  caps = effective_ranks(tree, leg_dims, want);
+  for (int u = 1; u < n; ++u) caps[u] = std::max(caps[u], ranks[u]);
+  cap_dims.assign(n, {0, 0, 0});
+  P_cap.assign(n, 0);
+  P_cap_max = 0;
+  r_cap_max = 1;
+  for (int u = 0; u < n; ++u) {
+    int64_t p = 1;
+    for (int i = 0; i < 3; ++i) {
+      const Leg& L = tree.legs[u][i];
+      int d = L.kind == 'p' ? caps[u] : L.kind == 'n' ? caps[L.v] : leg_dims[L.v];
+      cap_dims[u][i] = d;
+      p *= d;
+    }
+    P_cap[u] = p;
+    P_cap_max = std::max(P_cap_max, p);
+  }
+  for (int u = 1; u < n; ++u) r_cap_max = std::max(r_cap_max, caps[u]);
+  theta_cap = 1;
+  for (int c = 1; c < n; ++c) {  // merged pair (c, parent) at capacity: P_c * P_p / r_cap^2
+    const int p = tree.parent[c];
+    theta_cap = std::max(theta_cap, P_cap[c] / caps[c] * (P_cap[p] / caps[c]));
+  }
 }
 
 int Plan::dir_id(int a, int b) const {
@@ -303,6 +340,13 @@ std::string Plan::load_sop(int n_ops, const int32_t* opl, const int64_t* opo, co
   return "";
 }
 
+std::string Plan::rebuild_classes() {
+  std::string e = build_classes();
+  if (!e.empty()) return e;
+  compute_lambda();
+  return build_jobs();
+}
+
 void Plan::compute_lambda() {
   std::vector<double> opn(ops.size());
   for (size_t k = 0; k < ops.size(); ++k) opn[k] = spectral_norm(ops[k].data(), leg_dims[op_leg[k]]);
@@ -385,7 +429,7 @@ std::string Plan::build_classes() {
         if (a_in && p_out) cls.push_back(ClassId{1, k});
         if (!a_in && p_in) cls.push_back(ClassId{2, k});
       }
-      for (size_t i = 0; i < cls.size(); ++i) dir_slots[e].push_back(new_mat(ranks[c]));
+      for (size_t i = 0; i < cls.size(); ++i) dir_slots[e].push_back(new_mat(caps[c]));
     }
   }
   // open-leg matrices
@@ -430,7 +474,7 @@ std::string Plan::build_classes() {
     }
   }
   bond_mat = (int)mats.size();  // alias of the bond buffer (no pool storage)
-  mats.push_back(MatSlot{r_max, -1});
+  mats.push_back(MatSlot{r_cap_max, -1});
   return "";
 }
 
@@ -445,14 +489,15 @@ int Plan::add_list(const std::vector<ApOut>& outs, const std::vector<std::vector
   for (size_t i = 0; i < outs.size(); ++i) {
     ApOut o = outs[i];
     o.term_begin = (int)ap_terms.size();
-    const int dd[3] = {o.d0, o.d1, o.d2};
+    if (o.d3 < 1) o.d3 = 1;
+    const int dd[4] = {o.d0, o.d1, o.d2, o.d3};
     for (const ApTerm& t : tl[i]) {
       ap_terms.push_back(t);
-      if (t.mat >= 0) L.flops += 8.0 * o.d0 * o.d1 * o.d2 * dd[t.leg];
+      if (t.mat >= 0) L.flops += 8.0 * o.d0 * o.d1 * o.d2 * o.d3 * dd[t.leg];
     }
     o.term_end = (int)ap_terms.size();
     o.tile0 = tiles;
-    int64_t p = (int64_t)o.d0 * o.d1 * o.d2;
+    int64_t p = (int64_t)o.d0 * o.d1 * o.d2 * o.d3;
     tiles += (int)((p + kApTile - 1) / kApTile);
     ap_outs.push_back(o);
   }
@@ -480,34 +525,54 @@ int Plan::add_pj_list(const std::vector<PjOut>& outs) {
   return (int)pj_lists.size() - 1;
 }
 
-// Node-centre operator of node u: singles {S_l on l} and pairs (X slot, l1, P slot, l2).
-void Plan::node_terms(int u, int src, int, std::vector<ApTerm>& singles,
-                      std::vector<std::array<int, 4>>& pairs) const {
+// Operator on a list of virtual legs (node, leg index): singles {S on each leg}
+// and pairs (X slot, leg a, P slot, leg b) for every key whose factor lies
+// behind leg a and whose partners lie behind leg b. The legs' behind-sets must
+// partition the open legs (one node's three legs, or a merged pair's four).
+void Plan::vl_terms(const std::vector<std::pair<int, int>>& vl, int src, std::vector<ApTerm>& singles,
+                    std::vector<std::array<int, 4>>& pairs) const {
   singles.clear();
   pairs.clear();
-  std::array<std::vector<char>, 3> B;
-  for (int li = 0; li < 3; ++li) B[li] = behind(u, li);
-  for (int li = 0; li < 3; ++li) {
-    int s = slot_of(u, li, ClassId{0, -1});
-    if (s >= 0) singles.push_back(ApTerm{s, li, src, 0});
+  const int nv = (int)vl.size();
+  std::vector<std::vector<char>> B(nv);
+  for (int a = 0; a < nv; ++a) B[a] = behind(vl[a].first, vl[a].second);
+  for (int a = 0; a < nv; ++a) {
+    int s = slot_of(vl[a].first, vl[a].second, ClassId{0, -1});
+    if (s >= 0) singles.push_back(ApTerm{s, a, src, 0});
   }
   std::vector<std::vector<char>> partner_on(keys.size(), std::vector<char>(tree.n_legs, 0));
   for (size_t m = 0; m < terms.size(); ++m)
     if (term_key[m] >= 0) partner_on[term_key[m]][terms[m].f[term_partner[m]].leg] = 1;
   for (size_t k = 0; k < keys.size(); ++k) {
     int l1 = -1;
-    for (int li = 0; li < 3; ++li)
-      if (B[li][keys[k].leg]) l1 = li;
-    for (int l2 = 0; l2 < 3; ++l2) {
+    for (int a = 0; a < nv; ++a)
+      if (B[a][keys[k].leg]) l1 = a;
+    for (int l2 = 0; l2 < nv; ++l2) {
       if (l2 == l1) continue;
       bool any = false;
       for (int l = 0; l < tree.n_legs; ++l) any = any || (partner_on[k][l] && B[l2][l]);
       if (!any) continue;
-      int xs = slot_of(u, l1, ClassId{1, (int)k});
-      int ps = slot_of(u, l2, ClassId{2, (int)k});
+      int xs = slot_of(vl[l1].first, vl[l1].second, ClassId{1, (int)k});
+      int ps = slot_of(vl[l2].first, vl[l2].second, ClassId{2, (int)k});
       pairs.push_back({xs, l1, ps, l2});
     }
   }
+}
+
+void Plan::node_terms(int u, int src, int, std::vector<ApTerm>& singles,
+                      std::vector<std::array<int, 4>>& pairs) const {
+  vl_terms({{u, 0}, {u, 1}, {u, 2}}, src, singles, pairs);
+}
+
+std::array<int, 4> Plan::theta_dims(int first, int second) const {
+  std::array<int, 4> d{1, 1, 1, 1};
+  int k = 0;
+  const int lf = tree.leg_index(first, second), ls = tree.leg_index(second, first);
+  for (int i = 0; i < 3; ++i)
+    if (i != lf) d[k++] = dims[first][i];
+  for (int i = 0; i < 3; ++i)
+    if (i != ls) d[k++] = dims[second][i];
+  return d;
 }
 
 std::string Plan::build_jobs() {
@@ -526,7 +591,11 @@ std::string Plan::build_jobs() {
   buf.bond_ys = n + 5;
   buf.bond_ys2 = n + 6;
   buf.bond_acc = n + 7;
-  buf.t0 = n + 8;
+  buf.th_y = n + 8;
+  buf.th_ys = n + 9;
+  buf.th_ys2 = n + 10;
+  buf.th_acc = n + 11;
+  buf.t0 = n + 12;
   // count pairs / classes to size T and W
   int max_pairs = 0, max_classes = 0;
   std::vector<ApTerm> singles;
@@ -562,6 +631,17 @@ std::string Plan::build_jobs() {
       bond_terms(dir ? p : c, dir ? c : p, 0, singles, pairs);
       max_pairs = std::max(max_pairs, (int)pairs.size());
     }
+  }
+  for (int c = 1; c < n; ++c) {  // two-site operators have more pairs (four legs)
+    int p = tree.parent[c];
+    std::vector<std::pair<int, int>> vl;
+    const int lf = tree.leg_index(c, p), ls = tree.leg_index(p, c);
+    for (int i = 0; i < 3; ++i)
+      if (i != lf) vl.push_back({c, i});
+    for (int i = 0; i < 3; ++i)
+      if (i != ls) vl.push_back({p, i});
+    vl_terms(vl, 0, singles, pairs);
+    max_pairs = std::max(max_pairs, (int)pairs.size());
   }
   buf.n_t = std::max(max_pairs, 1);
   buf.w0 = buf.t0 + buf.n_t;
@@ -618,6 +698,42 @@ std::string Plan::build_jobs() {
         for (size_t g = 0; g < pairs.size(); ++g)
           all.push_back(ApTerm{pairs[g][0], pairs[g][1], buf.t0 + (int)g, 0});
         bond_flow[e].combine[var] = add_list({base}, {all});
+      }
+    }
+  }
+  // two-site flows (ps2): Theta of the merged pair (first, second)
+  two_site.assign(2 * n, {});
+  for (int c = 1; c < n; ++c) {
+    int p = tree.parent[c];
+    for (int dir = 0; dir < 2; ++dir) {
+      int first = dir ? p : c, second = dir ? c : p;
+      int e = dir_id(first, second);
+      std::vector<std::pair<int, int>> vl;
+      const int lf = tree.leg_index(first, second), ls = tree.leg_index(second, first);
+      for (int i = 0; i < 3; ++i)
+        if (i != lf) vl.push_back({first, i});
+      for (int i = 0; i < 3; ++i)
+        if (i != ls) vl.push_back({second, i});
+      const std::array<int, 4> td = theta_dims(first, second);
+      for (int var = 0; var < 3; ++var) {
+        int src = var == 0 ? buf.th_y : var == 1 ? buf.th_ys : buf.th_ys2;
+        vl_terms(vl, src, singles, pairs);
+        ApOut base{td[0], td[1], td[2], 0, 0, -1, 0, td[3]};
+        if (!pairs.empty()) {
+          std::vector<ApOut> outs;
+          std::vector<std::vector<ApTerm>> tl;
+          for (size_t g = 0; g < pairs.size(); ++g) {
+            ApOut o = base;
+            o.dst = buf.t0 + (int)g;
+            outs.push_back(o);
+            tl.push_back({ApTerm{pairs[g][2], pairs[g][3], src, 0}});
+          }
+          two_site[e].first[var] = add_list(outs, tl);
+        }
+        std::vector<ApTerm> all = singles;
+        for (size_t g = 0; g < pairs.size(); ++g)
+          all.push_back(ApTerm{pairs[g][0], pairs[g][1], buf.t0 + (int)g, 0});
+        two_site[e].combine[var] = add_list({base}, {all});
       }
     }
   }

@@ -100,7 +100,7 @@ struct ApOut {
   int32_t term_begin, term_end;
   int32_t dst;      // buffer id (STORE epilogue) or -1 (epilogue from kernel args)
   int32_t tile0;    // first global tile of this output
-  int32_t pad;
+  int32_t d3;       // fourth leg (two-site tensors); 1 for node tensors
 };
 struct ApList {
   int32_t out_begin, out_end;  // into the global ApOut table
@@ -130,6 +130,7 @@ struct BufIds {
   int t0, n_t;            // pair intermediates T_0..T_{n_t-1}
   int w0, n_w;            // env class outputs W_0..W_{n_w-1}
   int bond_y, bond_ys, bond_ys2, bond_acc;  // bond matrices as (1, d, d) tensors
+  int th_y, th_ys, th_ys2, th_acc;          // two-site tensor Theta (ps2)
   int n_bufs;
 };
 
@@ -160,11 +161,18 @@ struct Plan {
   std::vector<int> term_key;      // key of a two-factor term (-1 otherwise)
   std::vector<int> term_partner;  // index of the partner factor in the term
 
-  // node dims (3 legs) and sizes
+  // node dims (3 legs) and sizes at the current ranks
   std::vector<std::array<int, 3>> dims;
   std::vector<int64_t> P;
   int64_t P_max = 0;
   int r_max = 0;
+  // capacity (workspace sizing): ranks capped at max(requested, max_rank)
+  std::vector<int> req, caps;
+  std::vector<std::array<int, 3>> cap_dims;
+  std::vector<int64_t> P_cap;
+  int64_t P_cap_max = 0, theta_cap = 0;
+  int r_cap_max = 1;
+  int cap_rank = 32;
 
   // classes
   std::vector<std::vector<ClassId>> dir_classes;  // per directed bond id
@@ -185,6 +193,9 @@ struct Plan {
   std::vector<FlowLists> bond_flow;          // per directed bond (from -> to)
   std::vector<EnvLists> env;                 // per directed bond
   std::vector<std::array<int, 3>> absorb;    // per node: ApList id for R on leg li
+  // ps2 two-site flows: per directed bond (first -> second), Theta legs = first's
+  // other legs then second's other legs (canonical order, bond removed)
+  std::vector<FlowLists> two_site;
 
   int dir_id(int a, int b) const;                 // a, b adjacent nodes
   std::vector<char> behind(int u, int li) const;  // open legs behind leg li of node u
@@ -196,6 +207,10 @@ struct Plan {
                        const double* op_data, int n_terms, const int32_t* term_offsets,
                        const int32_t* term_ops, const double* coef, const int32_t* coef_drive);
   void compute_lambda();
+  void set_caps(int max_rank);  // capacity ranks; rebuild classes afterwards
+  std::string rebuild_classes();  // after set_caps: classes, lambda, job lists
+  void update_dims();           // dims/P/P_max/r_max from ranks
+  std::array<int, 4> theta_dims(int first, int second) const;
   int n_sub(double tau, double kappa) const;
   bool built_jobs = false;
   std::string build_jobs();
@@ -207,6 +222,9 @@ struct Plan {
   int add_pj_list(const std::vector<PjOut>& outs);
   void node_terms(int u, int src, int t_base, std::vector<ApTerm>& singles,
                   std::vector<std::array<int, 4>>& pairs) const;
+  // operator terms on an arbitrary list of (node, leg) "virtual legs"
+  void vl_terms(const std::vector<std::pair<int, int>>& vl, int src, std::vector<ApTerm>& singles,
+                std::vector<std::array<int, 4>>& pairs) const;
 };
 
 constexpr int kApTile = 32;   // output elements per CTA of the apply kernel

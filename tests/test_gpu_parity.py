@@ -196,7 +196,7 @@ def test_overflow_is_reported_as_numeric_error(pkg):
     g.close()
 
 
-def test_vmf_and_ps2_status(pkg):
+def test_vmf_status(pkg):
     w = W.spin_boson_tt(depth=3, n_pade=1, rank=2)
     g = gpu_from(pkg, w)
     with pytest.raises(pkg.TTNError) as e:
@@ -287,3 +287,61 @@ def test_batched_instances_equal_individual_runs(pkg):
         assert np.array_equal(gb.ttn_rdm(), ga.ttn_rdm())
     for g in batch + alone:
         g.close()
+
+
+# ---------------------------------------------------------------------------
+# ps2 (adaptive rank): two-site flows, FP64 one-sided Jacobi SVD, truncation
+# r = min(cap, max(1, ceil(ps2_ratio * #{sigma > ps2_atol}))), deterministic
+# completion; ranks must follow the oracle exactly.
+# ---------------------------------------------------------------------------
+def run_ps2(pkg, w, n, max_rank, atol):
+    g = gpu_from(pkg, w, params={"max_rank": max_rank, "ps2_atol": atol})
+    o = ottn.from_workload(w, params=ottn.Params(ps2_atol=atol, max_rank=max_rank))
+    err = 0.0
+    for k in range(n):
+        g.ttn_step(w.dt, pkg.TTN_PS2, 1)
+        o.step(w.dt, "ps2")
+        err = max(err, float(np.max(np.abs(g.ttn_rdm() - o.rdm()))))
+        assert list(g.ttn_get_ranks()) == o.ranks, (k, list(g.ttn_get_ranks()), o.ranks)
+    return err, g, o
+
+
+@pytest.mark.parametrize("tree,rank", [("tt", 1), ("btt", 3)])
+def test_ps2_spin_boson(pkg, tree, rank):
+    w = W.spin_boson_tt(depth=4, n_pade=3, rank=rank, tree=tree)
+    err, g, o = run_ps2(pkg, w, 10, 8, 1e-7)
+    assert max(o.ranks) > rank  # the ranks did adapt
+    g.close()
+    assert err <= TOL_SHORT
+
+
+def test_ps2_driven_structured_bath(pkg):
+    w = W.driven_structured_tls(n_pade=1, depth=4)
+    err, g, o = run_ps2(pkg, w, 6, 6, 1e-6)
+    g.close()
+    assert err <= TOL_SHORT
+
+
+def test_ps2_multibath_and_reset(pkg):
+    w = W.exciton_chain(n_sites=3, rank=2, depth=3)
+    err, g, o = run_ps2(pkg, w, 4, 6, 1e-6)
+    assert err <= TOL_SHORT
+    # a new initial state restores the initial ranks
+    g.ttn_set_rdo0(w.rho0)
+    o2 = ottn.from_workload(w)
+    assert list(g.ttn_get_ranks()) == o2.ranks
+    assert np.max(np.abs(g.ttn_rdm() - w.rho0)) == 0.0
+    g.close()
+
+
+def test_ps2_then_ps1_mixed_strategy(pkg):
+    """Adaptive phase then fixed-rank phase on the ranks ps2 chose (the paper's
+    mixed strategy with ps1 as the main method)."""
+    w = W.spin_boson_tt(depth=4, n_pade=3, rank=2, tree="btt")
+    err, g, o = run_ps2(pkg, w, 5, 8, 1e-7)
+    for _ in range(5):
+        g.ttn_step(w.dt, pkg.TTN_PS1, 1)
+        o.step(w.dt, "ps1")
+        err = max(err, float(np.max(np.abs(g.ttn_rdm() - o.rdm()))))
+    g.close()
+    assert err <= TOL_SHORT

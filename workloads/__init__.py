@@ -249,9 +249,11 @@ def driven_structured_tls(n_steps: int = 2000, n_pade: int = 25, depth: int = 10
     parent, leg_node = balanced_binary(K)
     rho0 = np.zeros((2, 2), np.complex128)
     rho0[0, 0] = 1.0
+    # ps2 starts from the product state padded to rank 4: in a binary tree every
+    # two-site block of an all-rank-1 state has a rank-1 side, so ranks could not grow
     return Workload(name=f"driven TLS structured bath K={K} N={depth} cap={cap}",
                     H=0.75 * SIGMA_Z, baths=[bath], depth=[depth] * K, parent=parent,
-                    leg_node=leg_node, ranks=uniform_ranks(parent, 1), rho0=rho0,
+                    leg_node=leg_node, ranks=uniform_ranks(parent, 4), rho0=rho0,
                     dt=0.01, n_steps=n_steps, scheme="ps2",
                     drives=[Drive(V=SIGMA_X.copy(), amp=0.2, omega=1.5)],
                     ps2_atol=1e-6, ps2_ratio=2.0, max_rank=cap)
