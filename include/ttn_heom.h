@@ -206,6 +206,43 @@ ttn_status ttn_profile(ttn_t h, int32_t on);
 ttn_status ttn_profile_read(ttn_t h, int32_t kind, double* ms);
 ttn_status ttn_stats_reset(ttn_t h);
 
+/* Learned rank proposer (not in the paper). A fixed 24-64-64-13 MLP (ReLU,
+ * softmax over rank changes -4..+8) proposes, for every ps2 split, the new rank
+ * of the bond from the bond's history (features below); the split is then
+ * computed by a randomised range finder (Gaussian sketch of r + 8 columns,
+ * Householder QR, Jacobi SVD of the small projected matrix). The proposal is
+ * accepted only if the truncation rule applied to the sketch's singular values
+ * cuts inside the sketch and the exact discarded weight
+ * ||Theta||_F^2 - sum_{i<r} sigma_i^2 is at most ps2_atol^2; otherwise the full
+ * Jacobi SVD rule runs. Features (24 floats): log10 of the bond's last
+ * normalised singular values (16, /16, -1 if absent), rank / cap, log10 of the
+ * last 4 discarded weights (/20, -1 if absent), log10(ps2_atol)/10,
+ * ps2_ratio/4, 1. Parameters: one float vector (ttn_mlp_n_params entries) in
+ * the order W1, b1, W2, b2, W3, b3, matrices row-major (output index first).
+ *
+ * ttn_mlp_forward: logits[batch*13] for x[batch*24]; ws: ttn_mlp_workspace_size bytes.
+ * ttn_mlp_grad: mean softmax cross-entropy *loss (device float) and its gradient
+ *   grads[n_params] for integer labels in 0..12; deterministic (fixed-order sums).
+ * ttn_mlp_adam: one Adam step (beta 0.9/0.999, eps 1e-8, bias-corrected, t >= 1).
+ * All pointers are device pointers; work is issued on `stream`.
+ * ttn_split_log: the handle's log of full-SVD ps2 splits (features and the class
+ *   clamp(r_rule - r_before, -4, 8) + 4 the truncation rule chose); copies up to
+ *   max records to host arrays and returns the total in *n_total.
+ * ttn_set_rank_proposer: device parameters the handle reads at every ps2 split
+ *   (the caller keeps them alive; NULL turns the proposer off).
+ * ttn_proposer_stats: splits that consulted the network and proposals accepted. */
+ttn_status ttn_mlp_n_params(int32_t* n);
+ttn_status ttn_mlp_workspace_size(int32_t batch, size_t* bytes);
+ttn_status ttn_mlp_forward(const float* params, const float* x, int32_t batch, float* logits, void* ws,
+                           void* stream);
+ttn_status ttn_mlp_grad(const float* params, const float* x, const int32_t* labels, int32_t batch, float* grads,
+                        float* loss, void* ws, void* stream);
+ttn_status ttn_mlp_adam(float* params, float* m, float* v, const float* grads, int32_t t, float lr, void* stream);
+ttn_status ttn_split_log(ttn_t h, float* feats, int32_t* labels, int32_t max, int32_t* n_total);
+ttn_status ttn_split_log_clear(ttn_t h);
+ttn_status ttn_set_rank_proposer(ttn_t h, const float* params_dev);
+ttn_status ttn_proposer_stats(ttn_t h, int64_t* proposed, int64_t* accepted);
+
 /* No-allocation RDM. The paper has no counterpart to this entry point; it is
  * a deployment aid. Some callers cannot allocate device memory at all: code
  * running inside another framework's memory pool or arena, or runtimes that

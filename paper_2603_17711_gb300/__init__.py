@@ -18,7 +18,7 @@ from ._lib import (DRIVE_FN, TTN_FP64, TTN_MIXED_FP32, TTN_OK, TTN_PS1, TTN_PS2,
 from . import _lib
 
 __all__ = ["TTN", "TTNError", "heom", "TTN_FP64", "TTN_MIXED_FP32", "TTN_PS1", "TTN_PS2", "TTN_VMF",
-           "library", "from_model", "ttn_batch_step"]
+           "library", "from_model", "ttn_batch_step", "RankProposer"]
 
 _LIB: Optional[C.CDLL] = None
 
@@ -182,10 +182,118 @@ class TTN:
     def ttn_stats_reset(self) -> None:
         self._check(self.lib.ttn_stats_reset(self.h), "ttn_stats_reset")
 
+    def ttn_split_log(self):
+        """(features [n, 24] float32, classes [n] int32) of the full-SVD ps2 splits so far."""
+        n = C.c_int32()
+        self._check(self.lib.ttn_split_log(self.h, None, None, 0, C.byref(n)), "ttn_split_log")
+        f = np.zeros((n.value, 24), np.float32)
+        y = np.zeros(n.value, np.int32)
+        if n.value:
+            self._check(self.lib.ttn_split_log(self.h, f.ctypes.data_as(C.POINTER(C.c_float)), ptr(y, C.c_int32),
+                                               n.value, C.byref(n)), "ttn_split_log")
+        return f, y
+
+    def ttn_split_log_clear(self) -> None:
+        self._check(self.lib.ttn_split_log_clear(self.h), "ttn_split_log_clear")
+
+    def ttn_set_rank_proposer(self, proposer) -> None:
+        """Use a RankProposer's parameters at every ps2 split (None: off)."""
+        self._proposer = proposer
+        addr = proposer.params.data_ptr() if proposer is not None else None
+        self._check(self.lib.ttn_set_rank_proposer(self.h, C.c_void_p(addr)), "ttn_set_rank_proposer")
+
+    def ttn_proposer_stats(self):
+        a, b = C.c_int64(), C.c_int64()
+        self._check(self.lib.ttn_proposer_stats(self.h, C.byref(a), C.byref(b)), "ttn_proposer_stats")
+        return int(a.value), int(b.value)
+
     def ttn_substeps(self, tau: float) -> int:
         m = C.c_int32()
         self._check(self.lib.ttn_substeps(self.h, float(tau), C.byref(m)), "ttn_substeps")
         return int(m.value)
+
+
+class RankProposer:
+    """The 24-64-64-13 rank-proposer MLP: parameters and Adam state live in
+    CUDA tensors; forward, gradient and Adam run in the library's kernels."""
+
+    def __init__(self, seed: int = 0, params: Optional[np.ndarray] = None, device: int = 0):
+        import torch
+        n = C.c_int32()
+        library().ttn_mlp_n_params(C.byref(n))
+        self.n_params = int(n.value)
+        if params is None:
+            params = RankProposer.init_params(seed)
+        assert params.shape == (self.n_params,)
+        dev = torch.device("cuda", device)
+        self.params = torch.tensor(params, dtype=torch.float32, device=dev)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grads = torch.zeros_like(self.params)
+        self.t = 0
+        self.dev = dev
+
+    @staticmethod
+    def init_params(seed: int) -> np.ndarray:
+        """He-normal weights (std sqrt(2/fan_in)), zero biases, in the packed order."""
+        rng = np.random.default_rng(seed)
+        parts = []
+        for fan_out, fan_in in ((64, 24), (64, 64), (13, 64)):
+            parts.append(rng.normal(0.0, np.sqrt(2.0 / fan_in), size=fan_out * fan_in))
+            parts.append(np.zeros(fan_out))
+        return np.concatenate(parts).astype(np.float32)
+
+    def _ws(self, batch: int):
+        import torch
+        b = C.c_size_t()
+        library().ttn_mlp_workspace_size(batch, C.byref(b))
+        return torch.empty(int(b.value) // 4 + 1, dtype=torch.float32, device=self.dev)
+
+    def forward(self, x):
+        import torch
+        x = torch.as_tensor(np.ascontiguousarray(x, np.float32), device=self.dev)
+        B = x.shape[0]
+        z = torch.empty(B, 13, dtype=torch.float32, device=self.dev)
+        ws = self._ws(B)
+        st = library().ttn_mlp_forward(C.c_void_p(self.params.data_ptr()), C.c_void_p(x.data_ptr()), B,
+                                       C.c_void_p(z.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                       C.c_void_p(torch.cuda.current_stream(self.dev).cuda_stream))
+        if st != TTN_OK:
+            raise TTNError(st, "ttn_mlp_forward")
+        return z
+
+    def grad(self, x, y):
+        import torch
+        x = torch.as_tensor(np.ascontiguousarray(x, np.float32), device=self.dev)
+        y = torch.as_tensor(np.ascontiguousarray(y, np.int32), device=self.dev)
+        B = x.shape[0]
+        loss = torch.zeros(1, dtype=torch.float32, device=self.dev)
+        ws = self._ws(B)
+        st = library().ttn_mlp_grad(C.c_void_p(self.params.data_ptr()), C.c_void_p(x.data_ptr()),
+                                    C.c_void_p(y.data_ptr()), B, C.c_void_p(self.grads.data_ptr()),
+                                    C.c_void_p(loss.data_ptr()), C.c_void_p(ws.data_ptr()),
+                                    C.c_void_p(torch.cuda.current_stream(self.dev).cuda_stream))
+        if st != TTN_OK:
+            raise TTNError(st, "ttn_mlp_grad")
+        return loss, self.grads
+
+    def adam(self, lr: float) -> None:
+        import torch
+        self.t += 1
+        st = library().ttn_mlp_adam(C.c_void_p(self.params.data_ptr()), C.c_void_p(self.m.data_ptr()),
+                                    C.c_void_p(self.v.data_ptr()), C.c_void_p(self.grads.data_ptr()), self.t,
+                                    float(lr), C.c_void_p(torch.cuda.current_stream(self.dev).cuda_stream))
+        if st != TTN_OK:
+            raise TTNError(st, "ttn_mlp_adam")
+
+    def train(self, feats, labels, steps: int = 300, lr: float = 3e-3):
+        """Full-batch Adam on (features, classes); returns the loss history."""
+        hist = []
+        for _ in range(steps):
+            loss, _ = self.grad(feats, labels)
+            self.adam(lr)
+            hist.append(loss)
+        return [float(l.item()) for l in hist]
 
 
 def ttn_batch_step(handles: Sequence["TTN"], dt: float, scheme: int = TTN_PS1, n_steps: int = 1) -> None:

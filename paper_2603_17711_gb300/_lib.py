@@ -65,6 +65,16 @@ SIGNATURES = [
     ("ttn_stats_reset", C.c_int, [_h]),
     ("ttn_rdm_noalloc", C.c_int, [C.POINTER(ttn_tree), _i32p, _i32p, C.POINTER(C.c_void_p), C.c_void_p,
                                   C.c_void_p, C.c_char_p, C.c_size_t]),
+    ("ttn_mlp_n_params", C.c_int, [_i32p]),
+    ("ttn_mlp_workspace_size", C.c_int, [C.c_int32, C.POINTER(C.c_size_t)]),
+    ("ttn_mlp_forward", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("ttn_mlp_grad", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_void_p]),
+    ("ttn_mlp_adam", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p]),
+    ("ttn_split_log", C.c_int, [_h, C.POINTER(C.c_float), _i32p, C.c_int32, _i32p]),
+    ("ttn_split_log_clear", C.c_int, [_h]),
+    ("ttn_set_rank_proposer", C.c_int, [_h, C.c_void_p]),
+    ("ttn_proposer_stats", C.c_int, [_h, _i64p, _i64p]),
     ("ttn_last_error", C.c_char_p, [_h]),
     ("ttn_destroy", None, [_h]),
 ]

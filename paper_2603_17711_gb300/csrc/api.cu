@@ -58,6 +58,17 @@ struct ttn_ctx {
   int* svd_info = nullptr;
   std::vector<double> discarded;  // discarded weight of every ps2 split (host log)
   std::vector<int> init_ranks;
+  // learned rank proposer
+  const float* proposer = nullptr;  // device parameters (caller-owned), nullptr = off
+  int64_t n_proposed = 0, n_accepted = 0;
+  std::vector<float> log_feats;     // split records: 24 features each
+  std::vector<int32_t> log_labels;  // class = clamp(r_svd - r_cur, -4, 8) + 4
+  std::vector<std::vector<double>> edge_sig;   // per child node: last normalised spectrum (top 16)
+  std::vector<std::vector<double>> edge_disc;  // per child node: last discarded weights (newest first)
+  double2 *rs_omega = nullptr, *rs_Y = nullptr, *rs_B = nullptr;
+  float *mlp_x = nullptr, *mlp_ws = nullptr, *mlp_logits = nullptr;
+  double* rs_norm = nullptr;
+  uint64_t n_splits = 0;
   double2* rdm_vec = nullptr;
   double2* rho_dev = nullptr;
   int* flag_dev = nullptr;
@@ -162,7 +173,7 @@ ttn_status cuda_fail(ttn_t h, cudaError_t e, const char* what) {
 struct Layout {
   size_t nodes, pool, scratch, qr, rdm, rho, bufs_tab, mats_tab, terms, outs, pjs, drives, flag, total;
   size_t nodes32 = 0, pool32 = 0, scratch32 = 0, bufs_tab_lo = 0, mats_tab_lo = 0;  // FP32 mode only
-  size_t svd_small = 0;
+  size_t svd_small = 0, rsvd = 0, mlp = 0;
   std::vector<int64_t> node_off;  // complex elements from `nodes`
   std::vector<int64_t> rdm_off;
   int64_t scratch_elems = 0, qr_elems = 0, rdm_elems = 0;
@@ -208,6 +219,8 @@ Layout layout_of(const Plan& p, int prec) {
   L.pjs = take(p.pj_outs.size() * sizeof(PjOut));
   L.drives = take(p.locals.size() * sizeof(DriveMat));
   L.svd_small = take(p.theta_cap * sizeof(double) + (p.theta_cap + 4) * sizeof(int));
+  L.rsvd = take(3 * p.theta_cap * sizeof(double2));
+  L.mlp = take((24 + 13 + mlp_ws_floats(1) + 8) * sizeof(float) + 2 * sizeof(double));
   L.flag = take(sizeof(int) * 4);
   if (prec == PREC_F32) {
     L.nodes32 = take(acc * sizeof(float2));
@@ -393,37 +406,125 @@ struct Exec {
     });
     rk4(p.two_site[p.dir_id(first, second)], tl, p.buf.th_ys, p.buf.th_ys2, p.buf.th_acc, hh);
     const int nc = std::min(m, n), nr = std::max(m, n);
-    run(2, 0.0, [&] {
-      launch_jacobi_svd(h->h_bufs[tl], m, n, h->svd_A, h->svd_V, h->svd_sigma, h->svd_info, s);
-    });
-    std::vector<double> sig(nc);
-    int info[2] = {0, 0};
-    note(cudaMemcpyAsync(sig.data(), h->svd_sigma, nc * sizeof(double), cudaMemcpyDeviceToHost, s));
-    note(cudaMemcpyAsync(info, h->svd_info, sizeof(info), cudaMemcpyDeviceToHost, s));
-    note(cudaStreamSynchronize(s));
-    if (err != cudaSuccess) return;
-    h->n_flops[2] += 8.0 * 4.0 * info[0] * 0.5 * nc * (nc - 1) * (double)(nr + nc);
-    // truncation (host): r0 = #{sigma > ps2_atol}, r = min(cap, max(1, ceil(ratio r0)))
-    std::vector<int> perm(nc);
-    for (int i = 0; i < nc; ++i) perm[i] = i;
-    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return sig[a] > sig[b]; });
-    int r0 = 0;
-    for (int i = 0; i < nc; ++i) r0 += sig[i] > h->params.ps2_atol ? 1 : 0;
+    const int child = p.tree.parent[first] == second ? first : second;
+    const int r_cur = p.ranks[child];
     const int cap = std::min(h->params.max_rank, nc);
-    const int r = std::min(cap, std::max(1, (int)std::ceil(h->params.ps2_ratio * r0 - 1e-9)));
-    const double smax = sig[perm[0]];
-    int g = 0;
-    while (g < r && smax > 0 && sig[perm[g]] > h->params.svd_tol * smax) ++g;
-    double disc = 0.0;
-    for (int i = r; i < nc; ++i) disc += sig[perm[i]] * sig[perm[i]];
-    h->discarded.push_back(std::sqrt(disc));
-    note(cudaMemcpy(h->svd_perm, perm.data(), r * sizeof(int), cudaMemcpyHostToDevice));
+    // features of this split (history of the bond), computed before any SVD
+    float f[24];
+    {
+      const auto& es = h->edge_sig[child];
+      for (int i = 0; i < 16; ++i)
+        f[i] = i < (int)es.size() ? (float)(std::log10(std::max(es[i], 1e-16)) / 16.0) : -1.f;
+      f[16] = (float)r_cur / (float)cap;
+      const auto& ed = h->edge_disc[child];
+      for (int i = 0; i < 4; ++i)
+        f[17 + i] = i < (int)ed.size() ? (float)(std::log10(std::max(ed[i], 1e-20)) / 20.0) : -1.f;
+      f[21] = (float)(std::log10(std::max(h->params.ps2_atol, 1e-300)) / 10.0);
+      f[22] = (float)(h->params.ps2_ratio / 4.0);
+      f[23] = 1.f;
+    }
     const bool iso_first = centre_to == second;
     const int rows_iso = iso_first ? m : n;
-    run(3, 0.0, [&] {
-      launch_svd_vecs(h->svd_A, h->svd_V, h->svd_sigma, m, n, h->svd_perm, r, g, iso_first, h->svd_Z, h->svd_Zg,
-                      h->svd_C, s);
-    });
+    std::vector<double> sig;
+    std::vector<int> perm;
+    int r = 0, g = 0;
+    bool accepted = false;
+    if (h->proposer) {  // proposal -> randomised truncated factorisation, checked exactly
+      ++h->n_proposed;
+      float logits[13];
+      note(cudaMemcpyAsync(h->mlp_x, f, sizeof(f), cudaMemcpyHostToDevice, s));
+      run(3, 0.0, [&] { launch_mlp_forward(h->proposer, h->mlp_x, 1, h->mlp_ws, h->mlp_logits, s); });
+      note(cudaMemcpyAsync(logits, h->mlp_logits, sizeof(logits), cudaMemcpyDeviceToHost, s));
+      note(cudaStreamSynchronize(s));
+      int best = 0;
+      for (int o = 1; o < 13; ++o)
+        if (logits[o] > logits[best]) best = o;
+      const int r_prop = std::max(1, std::min(cap, r_cur + best - 4));
+      const int kk = std::min(r_prop + 8, nc);
+      if (kk < nc && err == cudaSuccess) {
+        run(3, 0.0, [&] { launch_gauss(h->rs_omega, (int64_t)n * kk, 0x5eedull + 7919ull * h->n_splits, s); });
+        run(2, 8.0 * m * n * kk, [&] { launch_zgemm(h->h_bufs[tl], h->rs_omega, h->rs_Y, m, kk, n, false, s); });
+        run(2, 0.0, [&] {
+          launch_qr(h->rs_Y, m, 1, kk, 2, h->params.qr_tol, h->qr_work, h->h_bufs[p.buf.tmp], h->svd_V, h->flag_dev,
+                    nullptr, nullptr, s);
+        });
+        run(2, 8.0 * m * n * kk, [&] { launch_zgemm(h->rs_Y, h->h_bufs[tl], h->rs_B, kk, n, m, true, s); });
+        run(2, 0.0, [&] { launch_jacobi_svd(h->rs_B, kk, n, h->svd_A, h->svd_V, h->svd_sigma, h->svd_info, s); });
+        run(3, 0.0, [&] { launch_norm2(h->h_bufs[tl], (int64_t)m * n, h->rs_norm, s); });
+        std::vector<double> sb(kk);
+        double tot = 0.0;
+        note(cudaMemcpyAsync(sb.data(), h->svd_sigma, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+        note(cudaMemcpyAsync(&tot, h->rs_norm, sizeof(double), cudaMemcpyDeviceToHost, s));
+        note(cudaStreamSynchronize(s));
+        std::vector<int> pb(kk);
+        for (int i = 0; i < kk; ++i) pb[i] = i;
+        std::stable_sort(pb.begin(), pb.end(), [&](int a, int b) { return sb[a] > sb[b]; });
+        int r0b = 0;
+        for (int i = 0; i < kk; ++i) r0b += sb[i] > h->params.ps2_atol ? 1 : 0;
+        const int rb = std::min(cap, std::max(1, (int)std::ceil(h->params.ps2_ratio * r0b - 1e-9)));
+        double kept = 0.0;
+        for (int i = 0; i < rb; ++i) kept += sb[pb[i]] * sb[pb[i]];
+        // accept only if the cut is resolved inside the sketch and the exact discarded
+        // weight ||Theta||_F^2 - sum_{i<r} sigma_i^2 is within ps2_atol^2
+        if (rb < kk && tot - kept <= h->params.ps2_atol * h->params.ps2_atol) {
+          accepted = true;
+          ++h->n_accepted;
+          r = rb;
+          const double smax = sb[pb[0]];
+          while (g < r && smax > 0 && sb[pb[g]] > h->params.svd_tol * smax) ++g;
+          h->discarded.push_back(std::sqrt(std::max(tot - kept, 0.0)));
+          sig.assign(sb.begin(), sb.end());
+          perm = pb;
+          note(cudaMemcpy(h->svd_perm, perm.data(), r * sizeof(int), cudaMemcpyHostToDevice));
+          run(3, 0.0, [&] {
+            launch_rsvd_vecs(h->rs_Y, m, kk, h->svd_A, h->svd_V, h->svd_sigma, n, h->svd_perm, r, g, iso_first,
+                             h->svd_Z, h->svd_Zg, h->svd_C, s);
+          });
+        }
+      }
+    }
+    if (!accepted) {
+      run(2, 0.0, [&] {
+        launch_jacobi_svd(h->h_bufs[tl], m, n, h->svd_A, h->svd_V, h->svd_sigma, h->svd_info, s);
+      });
+      sig.assign(nc, 0.0);
+      int info[2] = {0, 0};
+      note(cudaMemcpyAsync(sig.data(), h->svd_sigma, nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+      note(cudaMemcpyAsync(info, h->svd_info, sizeof(info), cudaMemcpyDeviceToHost, s));
+      note(cudaStreamSynchronize(s));
+      if (err != cudaSuccess) return;
+      h->n_flops[2] += 8.0 * 4.0 * info[0] * 0.5 * nc * (nc - 1) * (double)(nr + nc);
+      // truncation (host): r0 = #{sigma > ps2_atol}, r = min(cap, max(1, ceil(ratio r0)))
+      perm.resize(nc);
+      for (int i = 0; i < nc; ++i) perm[i] = i;
+      std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return sig[a] > sig[b]; });
+      int r0 = 0;
+      for (int i = 0; i < nc; ++i) r0 += sig[i] > h->params.ps2_atol ? 1 : 0;
+      r = std::min(cap, std::max(1, (int)std::ceil(h->params.ps2_ratio * r0 - 1e-9)));
+      const double smax = sig[perm[0]];
+      while (g < r && smax > 0 && sig[perm[g]] > h->params.svd_tol * smax) ++g;
+      double disc = 0.0;
+      for (int i = r; i < nc; ++i) disc += sig[perm[i]] * sig[perm[i]];
+      h->discarded.push_back(std::sqrt(disc));
+      // training record: features and the rank change the SVD rule chose
+      for (int i = 0; i < 24; ++i) h->log_feats.push_back(f[i]);
+      h->log_labels.push_back(std::max(-4, std::min(8, r - r_cur)) + 4);
+      note(cudaMemcpy(h->svd_perm, perm.data(), r * sizeof(int), cudaMemcpyHostToDevice));
+      run(3, 0.0, [&] {
+        launch_svd_vecs(h->svd_A, h->svd_V, h->svd_sigma, m, n, h->svd_perm, r, g, iso_first, h->svd_Z,
+                        h->svd_Zg, h->svd_C, s);
+      });
+    }
+    ++h->n_splits;
+    {  // bond history for the next split's features
+      auto& es = h->edge_sig[child];
+      es.clear();
+      const double s1 = sig.empty() ? 0.0 : sig[perm[0]];
+      for (int i = 0; i < 16 && i < (int)perm.size(); ++i) es.push_back(s1 > 0 ? sig[perm[i]] / s1 : 0.0);
+      auto& ed = h->edge_disc[child];
+      ed.insert(ed.begin(), h->discarded.back());
+      if (ed.size() > 4) ed.resize(4);
+    }
     if (g < r) {  // deterministic completion of the undetermined directions (Householder, tol 0)
       run(2, 0.0, [&] {
         launch_qr(h->svd_Z, rows_iso, 1, r, 2, 0.0, h->qr_work, h->h_bufs[p.buf.tmp], h->svd_V, h->flag_dev,
@@ -431,7 +532,6 @@ struct Exec {
       });
       run(3, 0.0, [&] { launch_restore_cols(h->svd_Z, h->svd_Zg, rows_iso, r, g, s); });
     }
-    const int child = p.tree.parent[first] == second ? first : second;
     set_rank(child, r);
     const int nfd[3] = {p.dims[first][0], p.dims[first][1], p.dims[first][2]};
     const int nsd[3] = {p.dims[second][0], p.dims[second][1], p.dims[second][2]};
@@ -767,6 +867,15 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
     h->svd_sigma = (double*)(base + L.svd_small);
     h->svd_perm = (int*)(h->svd_sigma + p.theta_cap);
     h->svd_info = h->svd_perm + p.theta_cap;
+    h->rs_omega = (double2*)(base + L.rsvd);
+    h->rs_Y = h->rs_omega + p.theta_cap;
+    h->rs_B = h->rs_Y + p.theta_cap;
+    h->rs_norm = (double*)(base + L.mlp);
+    h->mlp_x = (float*)(h->rs_norm + 2);
+    h->mlp_logits = h->mlp_x + 24;
+    h->mlp_ws = h->mlp_logits + 16;
+    h->edge_sig.assign(p.tree.n_nodes, {});
+    h->edge_disc.assign(p.tree.n_nodes, {});
     const int64_t r2 = (int64_t)p.r_cap_max * p.r_cap_max;
     h->h_bufs[p.buf.bond_y] = nxt(r2);
     h->h_bufs[p.buf.bond_ys] = nxt(r2);
@@ -1150,6 +1259,36 @@ ttn_status ttn_stats_reset(ttn_t h) {
     h->n_flops[k] = 0;
     h->prof_ms[k] = 0;
   }
+  return TTN_OK;
+}
+
+ttn_status ttn_split_log(ttn_t h, float* feats, int32_t* labels, int32_t max, int32_t* n_total) {
+  if (!h || !n_total || max < 0) return TTN_EINVAL;
+  const int n = (int)h->log_labels.size();
+  *n_total = n;
+  const int k = std::min(n, (int)max);
+  if (feats && k > 0) std::memcpy(feats, h->log_feats.data(), (size_t)k * 24 * sizeof(float));
+  if (labels && k > 0) std::memcpy(labels, h->log_labels.data(), (size_t)k * sizeof(int32_t));
+  return TTN_OK;
+}
+
+ttn_status ttn_split_log_clear(ttn_t h) {
+  if (!h) return TTN_EINVAL;
+  h->log_feats.clear();
+  h->log_labels.clear();
+  return TTN_OK;
+}
+
+ttn_status ttn_set_rank_proposer(ttn_t h, const float* params_dev) {
+  if (!h) return TTN_EINVAL;
+  h->proposer = params_dev;
+  return TTN_OK;
+}
+
+ttn_status ttn_proposer_stats(ttn_t h, int64_t* proposed, int64_t* accepted) {
+  if (!h) return TTN_EINVAL;
+  if (proposed) *proposed = h->n_proposed;
+  if (accepted) *accepted = h->n_accepted;
   return TTN_OK;
 }
 

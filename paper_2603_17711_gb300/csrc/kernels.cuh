@@ -86,6 +86,15 @@ void launch_jacobi_svd(const double2* theta, int m, int n, double2* A, double2* 
 void launch_svd_vecs(const double2* A, const double2* V, const double* sigma, int m, int n, const int* perm, int r,
                      int g, bool iso_first, double2* Z, double2* Zg, double2* Cm, cudaStream_t s);
 void launch_restore_cols(double2* Z, const double2* Zg, int rows, int r, int g, cudaStream_t s);
+// rank-proposer network and the randomised factorisation (mlp.cu)
+size_t mlp_ws_floats(int B);
+void launch_mlp_forward(const float* P, const float* x, int B, float* ws, float* logits, cudaStream_t s);
+void launch_gauss(double2* O, int64_t n, uint64_t seed, cudaStream_t s);
+void launch_zgemm(const double2* A, const double2* B, double2* C, int M, int N, int K, bool conjA, cudaStream_t s);
+void launch_norm2(const double2* x, int64_t n, double* out, cudaStream_t s);
+void launch_rsvd_vecs(const double2* Q, int m, int kk, const double2* A, const double2* V, const double* sigma, int n,
+                      const int* perm, int r, int g, bool iso_first, double2* Z, double2* Zg, double2* Cm,
+                      cudaStream_t s);
 void launch_write_pair(double2* Uf, float2* Uf_lo, const int* fd, int lf, double2* Us, float2* Us_lo, const int* sd,
                        int ls, const double2* Z, const double2* Cm, int r, bool iso_first, cudaStream_t s);
 
