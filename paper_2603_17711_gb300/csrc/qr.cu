@@ -1,13 +1,28 @@
 // Householder QR of a node tensor spread over a thread-block cluster (FP64).
 //
-// On GB300 a single SM retires about 2 FP64 FMA per clock, so a one-CTA
-// Householder QR of a 400 x 20 complex matricisation takes ~170 us. Here the
-// m rows are split over C <= 16 CTAs of one cluster; each CTA keeps its row
-// block in shared memory and the per-column reductions (the column norm and the
-// dot products with the trailing columns) are exchanged through distributed
-// shared memory with two cluster barriers per column. Q is then formed from
-// the compact WY representation H_0..H_{n-1} = I - V T V^H (Schreiber-Van Loan),
-// which costs one Gram reduction instead of n sequential reflector passes.
+// GB300 retires FP64 at a small fraction of its FP32 rate: a warp issues one
+// FP64 instruction per ~64 cycles, an SM about one per ~19 cycles, and an FP64
+// square root or division costs ~600 cycles. The kernel is therefore laid out
+// to keep the number of FP64 warp instructions on the critical path small:
+//
+//  * the m rows are split over C <= 16 CTAs of one cluster, each keeping its
+//    row block in shared memory;
+//  * a column costs ONE exchange: every CTA pushes (st.async into the other
+//    CTAs' shared memory, completing bytes on their mbarrier) its partial
+//    squared norm of column j and its partial dots u_k = x_j^H a_k, k > j, and
+//    the CTA owning row j adds x_0 and row j of the trailing columns. With
+//    v = x + phi*alpha*e_0 the reflector dot is then w_k = sum u_k + alpha
+//    conj(phi) a_k[j], so norm and dots need no second round trip;
+//  * alpha, phi and beta are computed by one warp (two lanes share each sqrt
+//    and division) while the other warps sum the pushed dot partials;
+//  * the update and the next column's partials use groups of 8 lanes per
+//    trailing column (rows strided over the group), so each warp instruction
+//    covers 4 columns;
+//  * Q is formed from the compact WY form H_0..H_{n-1} = I - V T V^H, but
+//    instead of the sequential recurrence for T, M = T V_top^H is obtained by
+//    back substitution with T^{-1} = diag(1/beta) + strictly-upper(V^H V)
+//    (Joffrain, Low, Quintana-Orti, van de Geijn, Van Zee 2006), one column of
+//    M per warp, spread over the cluster.
 //
 // The arithmetic convention is the one of the CPU oracle and of the one-CTA
 // kernel: for column j with remainder x of norm alpha, alpha <= tol*||A||_F
@@ -15,7 +30,9 @@
 // v = x + phi*alpha*e_0, phi = x_0/|x_0| (1 if x_0 = 0), beta = 1/(alpha(alpha+|x_0|)),
 // and finally row j of R / column j of Q are rescaled by the phase -phi so
 // that diag(R) >= 0. All reductions run in a fixed order, so results are
-// bitwise reproducible.
+// bitwise reproducible. Every wait on a peer is bounded (2 s from the kernel
+// start): on expiry bit 2 of *flag is set and the kernel runs to its end
+// without further exchanges.
 #include <cooperative_groups.h>
 
 #include "kernels.cuh"
@@ -27,14 +44,13 @@ namespace ttn {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kNW = kThreads / 32;
+constexpr int kG = 8;                      // lanes per trailing-column group
+constexpr int kGPW = 32 / kG;              // column groups per warp
+constexpr int kSlots = (kNW - 1) * kGPW;   // column groups of warps 1..7
+constexpr int kMaxPass = (kQrClusterMaxN - 1 + kSlots - 1) / kSlots;
+constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ double2 cfma_c(double2 a, double2 b, double2 c) {  // a*b + c
-  c.x = fma(a.x, b.x, c.x);
-  c.x = fma(-a.y, b.y, c.x);
-  c.y = fma(a.x, b.y, c.y);
-  c.y = fma(a.y, b.x, c.y);
-  return c;
-}
 __device__ __forceinline__ double2 cfmaj(double2 a, double2 b, double2 c) {  // conj(a)*b + c
   c.x = fma(a.x, b.x, c.x);
   c.x = fma(a.y, b.y, c.x);
@@ -42,13 +58,23 @@ __device__ __forceinline__ double2 cfmaj(double2 a, double2 b, double2 c) {  // 
   c.y = fma(-a.y, b.x, c.y);
   return c;
 }
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {  // c - a*b
+  c.x = fma(-a.x, b.x, c.x);
+  c.x = fma(a.y, b.y, c.x);
+  c.y = fma(-a.x, b.y, c.y);
+  c.y = fma(-a.y, b.x, c.y);
+  return c;
+}
 __device__ __forceinline__ double wsum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
 }
-__device__ __forceinline__ double2 wsum2(double2 v) {
-  v.x = wsum(v.x);
-  v.y = wsum(v.y);
+// sum over aligned groups of kG lanes; every lane of a group gets the same bits
+__device__ __forceinline__ double2 gsum2(double2 v) {
+  for (int o = kG / 2; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(kFull, v.x, o);
+    v.y += __shfl_xor_sync(kFull, v.y, o);
+  }
   return v;
 }
 // block sum in a fixed order; every thread gets the result
@@ -64,14 +90,65 @@ __device__ double bsum(double v, double* red) {
   return s;
 }
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* mb, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mb)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* mb, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* mb, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(mb)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase of the given parity; false (and bit 2 of *flag) once the
+// kernel-wide deadline has passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mb, uint32_t parity, uint64_t deadline, int* flag) {
+  while (!mbar_try(mb, parity)) {
+    if (gtimer() > deadline) {
+      atomicOr(flag, 2);
+      return false;
+    }
+  }
+  return true;
+}
+// remote stores into another CTA's shared memory that complete bytes on its mbarrier
+__device__ __forceinline__ void push_f64(uint32_t raddr, double v, uint32_t rmb) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(raddr), "d"(v),
+               "r"(rmb)
+               : "memory");
+}
+__device__ __forceinline__ void push_c64(uint32_t raddr, double2 v, uint32_t rmb) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+               "d"(v.x), "d"(v.y), "r"(rmb)
+               : "memory");
+}
+
 }  // namespace
 
 // Shared-memory layout (dynamic, double2 units):
-//   A   [n][rp]  my row block, column-major (v_j overwrites rows >= j of column j)
-//   P2  [2][n]   per-parity partial dot products w_k
-//   G   [n][n]   partial Gram V^H V of my rows, then the full Gram
-//   T   [n][n]   WY factor
-//   MM  [n][n]   T V_top^H
+//   A   [n][rp]     my row block, column-major (v_j overwrites rows >= j of column j)
+//   SU  [2][16][n]  per-parity dot partials u_k pushed by each CTA
+//   RJ  [2][n]      per-parity row j of the trailing columns (from the owner of row j)
+//   G   [n][n]      partial strictly-upper Gram of my rows, later the gathered M
+//   GF  [n][n]      full strictly-upper Gram
+//   MM  [n][n]      the columns of M solved by this CTA
 __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int d1, int d2, int leg,
                                                          double tol, double2* R, int* flag, float2* U_lo,
                                                          float2* R_lo) {
@@ -87,22 +164,30 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
   const int r0 = me * rp;
   const int nr = max(0, min(m, r0 + rp) - r0);
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int lane = tid & 31, wid = tid >> 5;
+  const uint64_t deadline = gtimer() + 2000000000ull;
 
   extern __shared__ double2 smem[];
   double2* A = smem;
-  double2* P2 = A + (size_t)n * rp;
-  double2* G = P2 + 2 * n;
-  double2* T = G + n * n;
-  double2* MM = T + n * n;
-  __shared__ double red[kThreads / 32];
-  __shared__ double s_part[2];     // per-parity partial norm^2
-  __shared__ double2 s_x0[2];      // per-parity x_0 (owner of row j only)
+  double2* SU = A + (size_t)n * rp;
+  double2* RJ = SU + 32 * (size_t)n;
+  double2* G = RJ + 2 * (size_t)n;
+  double2* GF = G + (size_t)n * n;
+  double2* MM = GF + (size_t)n * n;
+  __shared__ __align__(8) uint64_t mb[2];
+  __shared__ double SN[2][16];
+  __shared__ double2 SX[2];
+  __shared__ double red[kNW];
+  __shared__ double s_part, s_frob;
   __shared__ double s_beta[kQrClusterMaxN], s_alpha[kQrClusterMaxN];
   __shared__ int s_skip[kQrClusterMaxN];
   __shared__ double2 s_phase[kQrClusterMaxN];
-  __shared__ double s_bcast[2];
-  __shared__ double2 s_bx0;
+  __shared__ double2 s_gam;
+  if (tid == 0) {
+    mbar_init(&mb[0], 1);
+    mbar_init(&mb[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
 
   // gather my rows: A[c][i] = U[.. row r0+i, column c ..]
   double fro = 0.0;
@@ -114,96 +199,158 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
       v = U[c * st[leg] + (int64_t)(r / dd[lb]) * st[la] + (int64_t)(r % dd[lb]) * st[lb]];
     }
     A[k] = v;
-    fro += v.x * v.x + v.y * v.y;
+    fro = fma(v.x, v.x, fma(v.y, v.y, fro));
   }
   fro = bsum(fro, red);
-  if (tid == 0) s_part[0] = fro;
-  cluster.sync();
+  if (tid == 0) s_part = fro;
+  cluster.sync();  // partial norms visible, mbarriers initialised cluster-wide
   if (wid == 0) {  // lane c reads CTA c's partial; fixed butterfly order
-    double v = lane < C ? *cluster.map_shared_rank(&s_part[0], lane) : 0.0;
+    double v = lane < C ? *cluster.map_shared_rank(&s_part, lane) : 0.0;
     v = wsum(v);
-    if (lane == 0) s_bcast[0] = sqrt(v);
+    if (lane == 0) s_frob = sqrt(v);
   }
   __syncthreads();
-  const double frob = s_bcast[0];
+  const double frob = s_frob;
   if (!isfinite(frob)) {  // uniform across the cluster
     if (tid == 0 && me == 0) atomicOr(flag, 1);
     cluster.sync();
     return;
   }
-  const double thr = tol * frob;
-  cluster.sync();  // everyone has read s_part[0] before it is reused
+  const double thr = tol * frob;  // s_part stays untouched until the final cluster barrier
+  bool alive = true;
 
-  for (int j = 0; j < n; ++j) {
-    const int par = j & 1;
-    double2* x = A + (size_t)j * rp;
-    const int i0 = max(0, j - r0);  // first local row with global index >= j
-    double ss = 0.0;
-    for (int i = i0 + tid; i < nr; i += nt) ss += x[i].x * x[i].x + x[i].y * x[i].y;
-    ss = bsum(ss, red);
-    const int owner = j / rp;
+  // Partials of step j over my rows >= j, pushed into every CTA's slots of
+  // parity j&1: ||x_j||^2 (warp 0), u_k = x_j^H a_k for k > j (column groups);
+  // the CTA owning row j also pushes x_0 and a_k[j].
+  auto push_partials = [&](int j) {
+    const int p = j & 1;
+    const int i0 = max(0, j - r0);
+    const double2* x = A + (size_t)j * rp;
+    const bool own = j >= r0 && j < r0 + nr;
+    const int lrow = j - r0;
     if (tid == 0) {
-      s_part[par] = ss;
-      if (owner == me) s_x0[par] = x[j - r0];
+      const uint32_t nk = (uint32_t)(n - j - 1);
+      mbar_arrive_tx(&mb[p], 8u * C + 16u * C * nk + (j < m ? 16u + 16u * nk : 0u));
     }
-    cluster.sync();
     if (wid == 0) {
-      double v = lane < C ? *cluster.map_shared_rank(&s_part[par], lane) : 0.0;
-      v = wsum(v);
-      if (lane == 0) {
-        s_bcast[1] = sqrt(v);
-        s_bx0 = *cluster.map_shared_rank(&s_x0[par], owner);
+      double ss = 0.0;
+      for (int i = i0 + lane; i < nr; i += 32) ss = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, ss));
+      ss = wsum(ss);
+      if (alive && lane < C) {
+        const uint32_t rmb = mapa(smem_u32(&mb[p]), lane);
+        push_f64(mapa(smem_u32(&SN[p][me]), lane), ss, rmb);
+        if (own) push_c64(mapa(smem_u32(&SX[p]), lane), x[lrow], rmb);
+      }
+    } else {
+      const int q = (wid - 1) * kGPW + (lane >> 3), sl = lane & (kG - 1);
+      for (int kb = j + 1; kb < n; kb += kSlots) {  // block-uniform trip count
+        const int k = kb + q;
+        const double2* a = A + (size_t)min(k, n - 1) * rp;
+        double2 u = make_double2(0.0, 0.0);
+        if (k < n)
+          for (int i = i0 + sl; i < nr; i += kG) u = cfmaj(x[i], a[i], u);
+        u = gsum2(u);
+        if (alive && k < n) {
+          const uint32_t su = smem_u32(&SU[((size_t)p * 16 + me) * n + k]);
+          const uint32_t rj = smem_u32(&RJ[(size_t)p * n + k]);
+          const uint32_t lmb = smem_u32(&mb[p]);
+          for (int c = sl; c < C; c += kG) {
+            const uint32_t rmb = mapa(lmb, c);
+            push_c64(mapa(su, c), u, rmb);
+            if (own) push_c64(mapa(rj, c), a[lrow], rmb);
+          }
+        }
+      }
+    }
+  };
+
+  // Column loop (see the header): wait for step j's partials, scalars in warp
+  // 0 / dot sums in warps 1..7, barrier, update, barrier, push step j+1.
+  // A push for step j+2 (same parity as j) can only leave a CTA after every
+  // CTA has pushed for step j+1, i.e. after all threads here have passed the
+  // second barrier of step j and are done with step j's slots and phase.
+  push_partials(0);
+  uint32_t ph[2] = {0u, 0u};
+  for (int j = 0; j < n; ++j) {
+    const int p = j & 1;
+    const int i0 = max(0, j - r0);
+    double2* x = A + (size_t)j * rp;
+    const bool own = j >= r0 && j < r0 + nr;
+    const int lrow = j - r0;
+    if (alive) alive = mbar_wait(&mb[p], ph[p], deadline, flag);
+    ph[p] ^= 1u;
+    double2 W[kMaxPass];
+    if (wid == 0) {
+      double a2 = lane < C ? SN[p][lane] : 0.0;  // C <= 16: lanes 0..15 carry the sum
+      for (int o = 8; o > 0; o >>= 1) a2 += __shfl_xor_sync(kFull, a2, o);
+      const double2 x0 = j < m ? SX[p] : make_double2(0.0, 0.0);
+      // lane 0: alpha = sqrt(sum), lane 1: |x_0| (one sqrt for both)
+      const double rt = sqrt(lane == 1 ? fma(x0.x, x0.x, x0.y * x0.y) : a2);
+      const double alpha = __shfl_sync(kFull, rt, 0);
+      const double ax0 = __shfl_sync(kFull, rt, 1);
+      if (!(alpha > thr)) {
+        for (int i = i0 + lane; i < nr; i += 32) x[i] = make_double2(0.0, 0.0);
+        if (lane == 0) {
+          s_skip[j] = 1;
+          s_beta[j] = 0.0;
+          s_alpha[j] = 0.0;
+          s_phase[j] = make_double2(1.0, 0.0);
+        }
+      } else {
+        // lane 0: 1/|x_0|, lane 1: beta (one division for both)
+        const double rc = 1.0 / (lane == 1 ? alpha * (alpha + ax0) : ax0);
+        const double inv = __shfl_sync(kFull, rc, 0);
+        const double beta = __shfl_sync(kFull, rc, 1);
+        const double2 phi = ax0 > 0.0 ? make_double2(x0.x * inv, x0.y * inv) : make_double2(1.0, 0.0);
+        if (lane == 0) {
+          s_skip[j] = 0;
+          s_beta[j] = beta;
+          s_alpha[j] = alpha;
+          s_phase[j] = make_double2(-phi.x, -phi.y);
+          s_gam = make_double2(alpha * phi.x, -alpha * phi.y);
+          if (own) x[lrow] = make_double2(fma(phi.x, alpha, x0.x), fma(phi.y, alpha, x0.y));
+        }
+      }
+    } else {
+      const int q = (wid - 1) * kGPW + (lane >> 3), sl = lane & (kG - 1);
+#pragma unroll
+      for (int ps = 0; ps < kMaxPass; ++ps) {
+        const int k = j + 1 + ps * kSlots + q;
+        if (j + 1 + ps * kSlots >= n) break;  // block-uniform
+        double2 w = make_double2(0.0, 0.0);
+        if (k < n)
+          for (int c = sl; c < C; c += kG) {
+            const double2 t = SU[((size_t)p * 16 + c) * n + k];
+            w.x += t.x;
+            w.y += t.y;
+          }
+        W[ps] = gsum2(w);
       }
     }
     __syncthreads();
-    const double alpha = s_bcast[1];
-    const double2 x0 = s_bx0;
-    if (alpha <= thr) {
-      for (int i = i0 + tid; i < nr; i += nt) x[i] = make_double2(0.0, 0.0);
-      if (tid == 0) {
-        s_skip[j] = 1;
-        s_beta[j] = 0.0;
-        s_alpha[j] = 0.0;
-        s_phase[j] = make_double2(1.0, 0.0);
-      }
-      __syncthreads();
-      continue;  // uniform: every CTA takes this branch
-    }
-    const double ax0 = hypot(x0.x, x0.y);
-    const double2 phi = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
-    const double beta = 1.0 / (alpha * (alpha + ax0));
-    if (tid == 0) {
-      if (owner == me) x[j - r0] = make_double2(x0.x + phi.x * alpha, x0.y + phi.y * alpha);
-      s_skip[j] = 0;
-      s_beta[j] = beta;
-      s_alpha[j] = alpha;
-      s_phase[j] = make_double2(-phi.x, -phi.y);
-    }
-    __syncthreads();
-    // partial dots w_k = sum_{my rows >= j} conj(v) a_k, one warp per column
-    double2* pw = P2 + par * n;
-    for (int k = j + 1 + wid; k < n; k += nw) {
-      const double2* a = A + (size_t)k * rp;
-      double2 w = make_double2(0.0, 0.0);
-      for (int i = i0 + lane; i < nr; i += 32) w = cfmaj(x[i], a[i], w);
-      w = wsum2(w);
-      if (lane == 0) pw[k] = w;
-    }
-    cluster.sync();
-    for (int k = j + 1 + wid; k < n; k += nw) {
-      double2 w = make_double2(0.0, 0.0);
-      if (lane < C) w = *cluster.map_shared_rank(&pw[k], lane);
-      w = wsum2(w);  // fixed butterfly order, identical in every CTA
-      const double2 bw = make_double2(beta * w.x, beta * w.y);
-      double2* a = A + (size_t)k * rp;
-      for (int i = i0 + lane; i < nr; i += 32) {
-        const double2 t = make_double2(x[i].x * bw.x - x[i].y * bw.y, x[i].x * bw.y + x[i].y * bw.x);
-        a[i] = make_double2(a[i].x - t.x, a[i].y - t.y);
+    if (wid > 0 && !s_skip[j]) {
+      const double beta = s_beta[j];
+      const double2 gam = s_gam;
+      const int q = (wid - 1) * kGPW + (lane >> 3), sl = lane & (kG - 1);
+#pragma unroll
+      for (int ps = 0; ps < kMaxPass; ++ps) {
+        const int k = j + 1 + ps * kSlots + q;
+        if (j + 1 + ps * kSlots >= n) break;
+        if (k < n) {
+          const double2 rj = RJ[(size_t)p * n + k];
+          double2 w = W[ps];
+          w.x = fma(gam.x, rj.x, fma(-gam.y, rj.y, w.x));
+          w.y = fma(gam.x, rj.y, fma(gam.y, rj.x, w.y));
+          const double2 bw = make_double2(beta * w.x, beta * w.y);
+          double2* a = A + (size_t)k * rp;
+          for (int i = i0 + sl; i < nr; i += kG) a[i] = cfms(x[i], bw, a[i]);
+        }
       }
     }
     __syncthreads();
+    if (j + 1 < n) push_partials(j + 1);
   }
-  cluster.sync();  // all reflectors final everywhere
+  cluster.sync();  // all reflectors final everywhere, every pushed slot consumed
 
   // R rows owned here (global rows < n), diag(R) = alpha >= 0 after the phase fix
   for (int k = tid; k < n * n; k += nt) {
@@ -220,84 +367,84 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
     R[k] = v;
     if (R_lo) R_lo[k] = make_float2((float)v.x, (float)v.y);
   }
-  // partial Gram G[a][b] = sum_{my rows} conj(v_a) v_b, v_a = 0 above the diagonal and for skipped a
-  for (int k = tid; k < n * n; k += nt) {
-    const int a = k / n, b = k % n;
+  // partial strictly-upper Gram of my rows, one thread per pair a < b
+  // (v_a vanishes above row a; skipped reflectors are zero columns)
+  const int npair = n * (n - 1) / 2;
+  for (int t = tid; t < npair; t += nt) {
+    int b = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);  // t = b(b-1)/2 + a
+    while (b * (b - 1) / 2 > t) --b;
+    while ((b + 1) * b / 2 <= t) ++b;
+    const int a = t - b * (b - 1) / 2;
     double2 g = make_double2(0.0, 0.0);
-    if (!s_skip[a] && !s_skip[b]) {
-      const int lo = max(max(a, b) - r0, 0);
-      const double2* va = A + (size_t)a * rp;
-      const double2* vb = A + (size_t)b * rp;
-      for (int i = lo; i < nr; ++i) g = cfmaj(va[i], vb[i], g);
-    }
-    G[k] = g;
+    const double2* va = A + (size_t)a * rp;
+    const double2* vb = A + (size_t)b * rp;
+    for (int i = max(b - r0, 0); i < nr; ++i) g = cfmaj(va[i], vb[i], g);
+    G[a * n + b] = g;
   }
   cluster.sync();
-  // full Gram (fixed order over CTAs) into T's storage temporarily
-  for (int k = tid; k < n * n; k += nt) {
-    double2 v[16];  // all remote loads in flight before the fixed-order sum
+  // full Gram: fixed-order sum of the CTAs' partials
+  for (int t = tid; t < npair; t += nt) {
+    int b = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
+    while (b * (b - 1) / 2 > t) --b;
+    while ((b + 1) * b / 2 <= t) ++b;
+    const int a = t - b * (b - 1) / 2;
+    double2 v[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = c < C ? cluster.map_shared_rank(G, c)[k] : make_double2(0.0, 0.0);
+    for (int c = 0; c < 16; ++c)
+      v[c] = c < C ? cluster.map_shared_rank(G, c)[a * n + b] : make_double2(0.0, 0.0);
     double2 g = make_double2(0.0, 0.0);
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      g.x += v[c].x;
-      g.y += v[c].y;
-    }
-    T[k] = g;
-  }
-  // gather V_top[c][b] = v_b[row c] for rows c < n into MM (remote reads)
-  for (int k = tid; k < n * n; k += nt) {
-    const int c = k / n, b = k % n;
-    double2 v = make_double2(0.0, 0.0);
-    if (!s_skip[b] && c >= b) {
-      const int own = c / rp;
-      v = cluster.map_shared_rank(A, own)[(size_t)b * rp + (c - own * rp)];
-    }
-    MM[k] = v;
-  }
-  cluster.sync();  // remote reads of G and A done; G may be overwritten
-  // WY factor: T[j][j] = beta_j, T[0:j, j] = -beta_j T[0:j, 0:j] Gram[0:j, j]
-  // (Gram in T's storage is copied to G first, T built in place column by column)
-  for (int k = tid; k < n * n; k += nt) G[k] = T[k];
-  __syncthreads();
-  for (int k = tid; k < n * n; k += nt) T[k] = make_double2(0.0, 0.0);
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (s_skip[j]) continue;
-    const double bj = s_beta[j];
-    for (int a = tid; a < j; a += nt) {
-      double2 acc = make_double2(0.0, 0.0);
-      for (int b = a; b < j; ++b) acc = cfma_c(T[a * n + b], G[b * n + j], acc);
-      T[a * n + j] = make_double2(-bj * acc.x, -bj * acc.y);
-    }
-    if (tid == 0) T[j * n + j] = make_double2(bj, 0.0);
-    __syncthreads();
-  }
-  // M = T V_top^H: M[a][c] = sum_b T[a][b] conj(V_top[c][b]); G's storage reused for M
-  for (int k = tid; k < n * n; k += nt) {
-    const int a = k / n, c = k % n;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int b = a; b < n; ++b) {
-      const double2 t = T[a * n + b], v = MM[c * n + b];
-      acc.x = fma(t.x, v.x, fma(t.y, v.y, acc.x));
-      acc.y = fma(t.y, v.x, fma(-t.x, v.y, acc.y));
-    }
-    G[k] = acc;
+    for (int c = 0; c < 16; ++c)
+      if (c < C) {
+        g.x += v[c].x;
+        g.y += v[c].y;
+      }
+    GF[a * n + b] = g;
   }
   __syncthreads();
-  // Q rows: Q[r][c] = delta_rc - sum_a v_a[r] M[a][c], column c scaled by phase_c, scattered to U
-  for (int k = tid; k < n * nr; k += nt) {
-    const int c = k / nr, i = k % nr;
+  // M = T V_top^H column by column: T^{-1} M[:, c] = conj(V_top[c, :])^T, with
+  // T^{-1} = diag(1/beta) + strictly-upper Gram; back substitution from a = c
+  // down (M[a][c] = 0 for a > c). Column c is solved by CTA c mod C, one warp.
+  for (int c = me + C * wid; c < n; c += C * kNW) {
+    double2 acc0 = make_double2(0.0, 0.0), acc1 = make_double2(0.0, 0.0);
+    if (c < m) {
+      const int oc = c / rp;
+      const double2* Ar = cluster.map_shared_rank(A, oc);
+      const int lr = c - oc * rp;
+      if (lane <= c && lane < n && !s_skip[lane]) {
+        const double2 v = Ar[(size_t)lane * rp + lr];
+        acc0 = make_double2(v.x, -v.y);
+      }
+      if (lane + 32 <= c && lane + 32 < n && !s_skip[lane + 32]) {
+        const double2 v = Ar[(size_t)(lane + 32) * rp + lr];
+        acc1 = make_double2(v.x, -v.y);
+      }
+    }
+    for (int a = c; a >= 0; --a) {
+      const double ba = s_beta[a];
+      const double2 src = a < 32 ? acc0 : acc1;
+      double2 ma = make_double2(ba * src.x, ba * src.y);
+      ma.x = __shfl_sync(kFull, ma.x, a & 31);
+      ma.y = __shfl_sync(kFull, ma.y, a & 31);
+      if (lane == (a & 31)) MM[a * n + c] = ma;
+      if (lane < a) acc0 = cfms(GF[lane * n + a], ma, acc0);
+      if (a > 32 && lane + 32 < a) acc1 = cfms(GF[(lane + 32) * n + a], ma, acc1);
+    }
+    for (int a = c + 1 + lane; a < n; a += 32) MM[a * n + c] = make_double2(0.0, 0.0);
+  }
+  cluster.sync();  // every column of M solved; partial Grams no longer read
+  // gather M into G (column c from CTA c mod C)
+  for (int t = tid; t < n * n; t += nt) G[t] = cluster.map_shared_rank(MM, (t % n) % C)[t];
+  __syncthreads();
+  // Q rows: Q[r][c] = delta_rc - sum_{a <= min(r,c)} v_a[r] M[a][c], column c scaled by phase_c
+  const int nch = (nr + 31) / 32;
+  for (int task = wid; task < n * nch; task += kNW) {
+    const int c = task / nch, i = (task % nch) * 32 + lane;
+    if (i >= nr) continue;
     const int r = r0 + i;
     double2 q = make_double2(r == c ? 1.0 : 0.0, 0.0);
-    for (int a = 0; a < n && a <= r; ++a) {
-      if (s_skip[a]) continue;
-      const double2 v = A[(size_t)a * rp + i];
-      const double2 mm = G[a * n + c];
-      q.x -= v.x * mm.x - v.y * mm.y;
-      q.y -= v.x * mm.y + v.y * mm.x;
-    }
+    const int amax = min(c, r);
+    for (int a = 0; a <= amax; ++a) q = cfms(A[(size_t)a * rp + i], G[a * n + c], q);
     const double2 p = s_phase[c];
     const double2 qp = make_double2(q.x * p.x - q.y * p.y, q.x * p.y + q.y * p.x);
     const int64_t at = c * st[leg] + (int64_t)(r / dd[lb]) * st[la] + (int64_t)(r % dd[lb]) * st[lb];
@@ -309,7 +456,7 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
 
 size_t qr_cluster_smem(int m, int n, int C) {
   const int rp = (m + C - 1) / C;
-  return sizeof(double2) * ((size_t)n * rp + 2 * n + 3 * (size_t)n * n);
+  return sizeof(double2) * ((size_t)n * rp + 34 * (size_t)n + 3 * (size_t)n * n);
 }
 
 int qr_cluster_size(int m, int n) {
