@@ -239,6 +239,8 @@ def bench_ours(args, rank, world, local_rank):
     if not args.no_batch:
         bws = W.spin_boson_batch(n=args.batch)
         hs = [make_gpu(pkg, bw, local_rank) for bw in bws]
+        for hh in hs:  # concurrent instances fill the GPU: one CTA per output tile
+            hh.ttn_set_params(max_split=1)
         pkg.ttn_batch_step(hs, 0.01, 1, args.warmup)
         torch.cuda.synchronize()
         s0 = hs[0].stream

@@ -86,7 +86,13 @@ typedef struct {
  *  ps2_ratio (2)     ... and then min(cap, max(1, ceil(ps2_ratio * r0))) values.
  *  max_rank  (32)    ps2 bond-rank cap (Sec. 5.3, max_auxiliary_rank).
  *  svd_tol   (1e-12) kept singular values <= svd_tol*sigma_1 are replaced by a
- *                    deterministic completion with zero weight. */
+ *                    deterministic completion with zero weight.
+ *  max_split (8)     1..8: at most this many CTAs (one thread-block cluster)
+ *                    share one output tile of a contraction launch; launches
+ *                    smaller than two CTAs per SM are split up to this factor
+ *                    (no counterpart in the paper: GB300 work distribution).
+ *                    Use 1 for instances advanced concurrently by
+ *                    ttn_batch_step, which fill the GPU by themselves. */
 typedef struct {
   double qr_tol;
   double kappa;
@@ -94,6 +100,7 @@ typedef struct {
   double ps2_ratio;
   int32_t max_rank;
   double svd_tol;
+  int32_t max_split;
 } ttn_params;
 
 /* Create a handle (Sec. 2.3, Eq. omega_tensor). leg_dims[n_legs]: leg

@@ -32,7 +32,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct ttn_ctx {
   Plan plan;
   int precision = TTN_FP64;
-  ttn_params params{1e-12, 2.5, 1e-7, 2.0, 32, 1e-12};
+  ttn_params params{1e-12, 2.5, 1e-7, 2.0, 32, 1e-12, kMaxSplit};
   bool sop_loaded = false;
   bool ws_bound = false;
   bool envs_dirty = true;
@@ -721,6 +721,14 @@ ttn_status ttn_create(const ttn_tree* tree, const int32_t* leg_dims, const int32
   ttn_t h = new (std::nothrow) ttn_ctx();
   if (!h) return TTN_ENOMEM;
   std::string e;
+  {  // SM count sizes the per-tile CTA split of the job lists; keep the default without a device
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+      h->plan.sm_count = sms;
+    else
+      cudaGetLastError();
+  }
   try {
     e = h->plan.build(tree->n_nodes, tree->parent, tree->n_legs, tree->leg_node, leg_dims, ranks);
   } catch (...) {
@@ -741,7 +749,7 @@ ttn_status ttn_set_params(ttn_t h, const ttn_params* prm) {
   return guarded(h, [&]() -> ttn_status {
     if (!prm) return h->fail(TTN_EINVAL, "null params");
     if (!(prm->qr_tol >= 0) || !(prm->kappa > 0) || !(prm->ps2_atol >= 0) || !(prm->ps2_ratio >= 1) ||
-        prm->max_rank < 1 || !(prm->svd_tol >= 0))
+        prm->max_rank < 1 || !(prm->svd_tol >= 0) || prm->max_split < 1 || prm->max_split > kMaxSplit)
       return h->fail(TTN_EINVAL, "parameter out of range");
     if (h->ws_bound && prm->max_rank != h->params.max_rank)
       return h->fail(TTN_ESTATE, "max_rank must be set before the workspace is bound");
@@ -753,8 +761,9 @@ ttn_status ttn_set_params(ttn_t h, const ttn_params* prm) {
         if (!e.empty()) return h->fail(TTN_EINVAL, e);
       }
     }
+    h->plan.set_split(prm->max_split);
     h->params = *prm;
-    h->drop_graph();  // substep counts and tolerances are baked into a captured step
+    h->drop_graph();  // substep counts, tolerances and launch shapes are baked into a captured step
     return TTN_OK;
   });
 }

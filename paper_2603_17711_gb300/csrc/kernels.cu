@@ -3,7 +3,11 @@
 // On GB300 the FP64 pipe issues about 2 FMA per SM per clock, so every kernel
 // here is bound by FP64 issue, not by memory: the data (node tensors of at most
 // a few hundred KB, environments of r x r) stays in L2 and L1.
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ttn {
 
@@ -64,13 +68,17 @@ template <> struct Cx<float> {
 
 // ---------------------------------------------------------------------------
 // Sum of mode products: out_o[idx] = sum_t M_t x_{leg_t} src_t.
-// A CTA owns 32 consecutive output elements (one per lane); its 8 warps split
-// the term list (warp w takes terms w, w+8, ...) and the partial sums are
-// added in a fixed order in shared memory, so results are bitwise
-// reproducible. In FP64 the bound is FP64 issue (~2 FMA/clk/SM): the mapping
-// spreads a node application over as many SMs as possible.
+// An output tile is 32 consecutive elements (one per lane). Its work is cut
+// into units -- an identity term, or kApChunk consecutive positions x of one
+// mode product -- dealt round-robin to the 8*k warps of the k CTAs (one
+// thread-block cluster) that share the tile. Each warp sums its units in
+// order, the CTA sums its warps in order, and CTA 0 of the cluster sums the
+// CTAs in order (through distributed shared memory), so results are bitwise
+// reproducible. GB300 issues one FP64 instruction per warp every ~64 cycles,
+// so short dependency chains (8 positions per unit, loads issued before the
+// FMAs) and many warps per tile are what makes a small contraction fast.
 // ---------------------------------------------------------------------------
-constexpr int kApWarps = 8;
+constexpr int kApWarps = kSplitWarps;
 
 // Leg geometry of one output element (kept in registers: selected by switch,
 // never indexed dynamically).
@@ -81,8 +89,19 @@ struct Geo {
 };
 
 template <typename R>
-__device__ __forceinline__ typename Cx<R>::T term_dot(const ApTerm& term, const DevTables& T, int64_t idx,
-                                                      const Geo& g) {
+__device__ __forceinline__ int term_dim(const ApTerm& term, const Geo& g) {
+  switch (term.leg) {
+    case 0: return g.d0;
+    case 1: return g.d1;
+    case 2: return g.d2;
+    default: return g.d3;
+  }
+}
+
+// contribution of positions [x0, x0 + kApChunk) of one term (the whole term if identity)
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::T unit_dot(const ApTerm& term, const DevTables& T, int64_t idx,
+                                                      const Geo& g, int x0) {
   using C = Cx<R>;
   using V = typename C::T;
   const V* __restrict__ src = (const V*)T.bufs[term.src];
@@ -98,17 +117,30 @@ __device__ __forceinline__ typename Cx<R>::T term_dot(const ApTerm& term, const 
   }
   const V* __restrict__ row = M + (int64_t)il * dl;
   const V* __restrict__ col = src + (idx - (int64_t)il * stride);
+  V mv[kApChunk], sv[kApChunk];
+#pragma unroll
+  for (int k = 0; k < kApChunk; ++k) {
+    const int x = x0 + k;
+    if (x < dl) {
+      mv[k] = row[x];
+      sv[k] = col[(int64_t)x * stride];
+    }
+  }
   V acc = C::zero();
-  for (int x = 0; x < dl; ++x) acc = C::fma(row[x], col[(int64_t)x * stride], acc);
+#pragma unroll
+  for (int k = 0; k < kApChunk; ++k)
+    if (x0 + k < dl) acc = C::fma(mv[k], sv[k], acc);
   return acc;
 }
 
 template <typename R>
-__global__ void __launch_bounds__(32 * kApWarps) k_apply(DevTables T, ApList L, Epi ep) {
+__global__ void __launch_bounds__(32 * kApWarps, 4) k_apply(DevTables T, ApList L, Epi ep) {
   using C = Cx<R>;
   using V = typename C::T;
   __shared__ V part[kApWarps][32];
-  const int tile = blockIdx.x;
+  __shared__ V slot[kMaxSplit][32];
+  const int K = L.k;
+  const int tile = blockIdx.x / K, rank = blockIdx.x % K;  // rank == block rank in the cluster
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int o = L.out_begin;
   while (o + 1 < L.out_end && T.outs[o + 1].tile0 <= tile) ++o;
@@ -126,14 +158,31 @@ __global__ void __launch_bounds__(32 * kApWarps) k_apply(DevTables T, ApList L, 
     g.i1 = (int)((idx / g.s1) % g.d1);
     g.i2 = (int)((idx / g.s2) % g.d2);
     g.i3 = (int)(idx % g.d3);
-    for (int t = out.term_begin + wid; t < out.term_end; t += kApWarps)
-      acc = C::add(acc, term_dot<R>(T.terms[t], T, idx, g));
+    const int W = K * kApWarps, me = rank * kApWarps + wid;
+    int u = 0;  // index of the term's first unit in the tile's unit list
+    for (int t = out.term_begin; t < out.term_end; ++t) {
+      const ApTerm term = T.terms[t];
+      const int nch = term.mat < 0 ? 1 : (term_dim<R>(term, g) + kApChunk - 1) / kApChunk;
+      for (int c = ((me - u) % W + W) % W; c < nch; c += W)
+        acc = C::add(acc, unit_dot<R>(term, T, idx, g, c * kApChunk));
+      u += nch;
+    }
   }
   part[wid][lane] = acc;
   __syncthreads();
+  if (wid == 0) {
+    acc = part[0][lane];
+    for (int w = 1; w < kApWarps; ++w) acc = C::add(acc, part[w][lane]);
+  }
+  if (K > 1) {
+    cg::cluster_group cluster = cg::this_cluster();
+    if (wid == 0 && rank > 0) cluster.map_shared_rank(&slot[0][0], 0)[rank * 32 + lane] = acc;
+    cluster.sync();
+    if (rank > 0) return;
+    if (wid == 0)
+      for (int r = 1; r < K; ++r) acc = C::add(acc, slot[r][lane]);
+  }
   if (wid != 0 || idx >= P) return;
-  acc = part[0][lane];
-  for (int w = 1; w < kApWarps; ++w) acc = C::add(acc, part[w][lane]);
   if (ep.mode == EPI_STORE) {
     ((V*)T.bufs[out.dst])[idx] = acc;
     return;
@@ -165,27 +214,54 @@ __global__ void __launch_bounds__(32 * kApWarps) k_apply(DevTables T, ApList L, 
   }
 }
 
+// Launch n_tiles * k CTAs; k > 1 makes every k consecutive CTAs one cluster.
+template <typename Kern, typename... Args>
+static void launch_split(Kern kern, int n_tiles, int k, cudaStream_t s, Args... args) {
+  if (k <= 1) {
+    kern<<<n_tiles, 32 * kSplitWarps, 0, s>>>(args...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_tiles * k), 1, 1);
+  cfg.blockDim = dim3(32 * kSplitWarps, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)k;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 void launch_apply(int prec, const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s) {
   if (L.n_tiles <= 0) return;
   if (prec == PREC_F32)
-    k_apply<float><<<L.n_tiles, 32 * kApWarps, 0, s>>>(T, L, e);
+    launch_split(k_apply<float>, L.n_tiles, L.k, s, T, L, e);
   else
-    k_apply<double><<<L.n_tiles, 32 * kApWarps, 0, s>>>(T, L, e);
+    launch_split(k_apply<double>, L.n_tiles, L.k, s, T, L, e);
 }
 
 // ---------------------------------------------------------------------------
 // Environment projection E[x', x] = sum_r conj(U[.. x' ..]) W[.. x ..] over all
-// legs except `leg`. A CTA owns 32 output entries (one per lane); its 8 warps
-// split the reduction range and are summed in a fixed order.
+// legs except `leg`. A tile is 32 output entries (one per lane); the reduction
+// range r is dealt round-robin to the 8*k warps of the k CTAs (one cluster)
+// sharing the tile, four positions per batch with loads issued first, and the
+// partial sums are added in a fixed order (warps, then CTAs via distributed
+// shared memory).
 // ---------------------------------------------------------------------------
-constexpr int kPjWarps = 8;
+constexpr int kPjWarps = kSplitWarps;
 
 template <typename R>
-__global__ void __launch_bounds__(32 * kPjWarps) k_project(DevTables T, PjList L) {
+__global__ void __launch_bounds__(32 * kPjWarps, 4) k_project(DevTables T, PjList L) {
   using C = Cx<R>;
   using V = typename C::T;
   __shared__ V part[kPjWarps][32];
-  const int tile = blockIdx.x;
+  __shared__ V slot[kMaxSplit][32];
+  const int K = L.k;
+  const int tile = blockIdx.x / K, rank = blockIdx.x % K;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int o = L.out_begin;
   while (o + 1 < L.out_end && T.pjs[o + 1].tile0 <= tile) ++o;
@@ -201,26 +277,48 @@ __global__ void __launch_bounds__(32 * kPjWarps) k_project(DevTables T, PjList L
   if (e < d * d) {
     const int xp = e / d, x = e % d;
     const V* __restrict__ U = (const V*)T.bufs[pj.u_buf] + (int64_t)xp * st[l];
-    const V* __restrict__ W = (const V*)T.bufs[pj.w_buf] + (int64_t)x * st[l];
-    for (int r = wid; r < nrest; r += kPjWarps) {
-      const int64_t off = (int64_t)(r / dd[lb]) * st[la] + (int64_t)(r % dd[lb]) * st[lb];
-      acc = C::fmaj(U[off], W[off], acc);
+    const V* __restrict__ Wt = (const V*)T.bufs[pj.w_buf] + (int64_t)x * st[l];
+    const int W = K * kPjWarps, me = rank * kPjWarps + wid;
+    for (int r0 = me; r0 < nrest; r0 += 4 * W) {
+      V uv[4], wv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = r0 + k * W;
+        if (r < nrest) {
+          const int64_t off = (int64_t)(r / dd[lb]) * st[la] + (int64_t)(r % dd[lb]) * st[lb];
+          uv[k] = U[off];
+          wv[k] = Wt[off];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (r0 + k * W < nrest) acc = C::fmaj(uv[k], wv[k], acc);
     }
   }
   part[wid][lane] = acc;
   __syncthreads();
+  if (wid == 0) {
+    acc = part[0][lane];
+    for (int w = 1; w < kPjWarps; ++w) acc = C::add(acc, part[w][lane]);
+  }
+  if (K > 1) {
+    cg::cluster_group cluster = cg::this_cluster();
+    if (wid == 0 && rank > 0) cluster.map_shared_rank(&slot[0][0], 0)[rank * 32 + lane] = acc;
+    cluster.sync();
+    if (rank > 0) return;
+    if (wid == 0)
+      for (int r = 1; r < K; ++r) acc = C::add(acc, slot[r][lane]);
+  }
   if (wid != 0 || e >= d * d) return;
-  acc = part[0][lane];
-  for (int w = 1; w < kPjWarps; ++w) acc = C::add(acc, part[w][lane]);
   ((V*)T.mats[pj.dst_mat])[e] = acc;
 }
 
 void launch_project(int prec, const DevTables& T, const PjList& L, cudaStream_t s) {
   if (L.n_tiles <= 0) return;
   if (prec == PREC_F32)
-    k_project<float><<<L.n_tiles, 32 * kPjWarps, 0, s>>>(T, L);
+    launch_split(k_project<float>, L.n_tiles, L.k, s, T, L);
   else
-    k_project<double><<<L.n_tiles, 32 * kPjWarps, 0, s>>>(T, L);
+    launch_split(k_project<double>, L.n_tiles, L.k, s, T, L);
 }
 
 // ---------------------------------------------------------------------------

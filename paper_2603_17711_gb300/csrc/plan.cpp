@@ -1,6 +1,8 @@
 // Host-side planning: see plan.hpp.
 #include "plan.hpp"
 
+#include <climits>
+
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -481,6 +483,22 @@ std::string Plan::build_classes() {
 // ---------------------------------------------------------------------------
 // Job lists
 // ---------------------------------------------------------------------------
+// CTAs per output tile: the smallest k <= min(useful, kMaxSplit) that brings
+// tiles * k to two CTAs per SM (1 when the list alone fills the device).
+int Plan::split_factor(int tiles, int useful) const {
+  const int target = 2 * sm_count;
+  int k = 1;
+  const int kmax = std::max(1, std::min(std::min(useful, kMaxSplit), max_split));
+  while (k < kmax && tiles * k < target) ++k;
+  return k;
+}
+
+void Plan::set_split(int m) {
+  max_split = m;
+  for (ApList& L : ap_lists) L.k = split_factor(L.n_tiles, L.useful);
+  for (PjList& L : pj_lists) L.k = split_factor(L.n_tiles, L.useful);
+}
+
 int Plan::add_list(const std::vector<ApOut>& outs, const std::vector<std::vector<ApTerm>>& tl) {
   ApList L;
   L.out_begin = (int)ap_outs.size();
@@ -503,6 +521,18 @@ int Plan::add_list(const std::vector<ApOut>& outs, const std::vector<std::vector
   }
   L.out_end = (int)ap_outs.size();
   L.n_tiles = tiles;
+  // Work units of an output tile: one per identity term, ceil(d_leg / kApChunk)
+  // per mode product. Split a tile over k CTAs (one cluster) while the grid is
+  // below two CTAs per SM and every warp still gets a unit.
+  int units_max = 1;
+  for (size_t i = 0; i < outs.size(); ++i) {
+    const int dd[4] = {outs[i].d0, outs[i].d1, outs[i].d2, outs[i].d3 < 1 ? 1 : outs[i].d3};
+    int u = 0;
+    for (const ApTerm& t : tl[i]) u += t.mat < 0 ? 1 : (dd[t.leg] + kApChunk - 1) / kApChunk;
+    units_max = std::max(units_max, u);
+  }
+  L.useful = (units_max + kSplitWarps - 1) / kSplitWarps;
+  L.k = split_factor(tiles, L.useful);
   ap_lists.push_back(L);
   return (int)ap_lists.size() - 1;
 }
@@ -521,6 +551,15 @@ int Plan::add_pj_list(const std::vector<PjOut>& outs) {
   }
   L.out_end = (int)pj_outs.size();
   L.n_tiles = tiles;
+  // split the reduction range so that each warp keeps at least 4 positions
+  int64_t rest_min = INT64_MAX;
+  for (const PjOut& o : outs) {
+    const int d = o.leg == 0 ? o.d0 : o.leg == 1 ? o.d1 : o.d2;
+    rest_min = std::min<int64_t>(rest_min, (int64_t)o.d0 * o.d1 * o.d2 / d);
+  }
+  if (outs.empty()) rest_min = 1;
+  L.useful = (int)std::min<int64_t>(kMaxSplit, std::max<int64_t>(1, rest_min / (4 * kSplitWarps)));
+  L.k = split_factor(tiles, L.useful);
   pj_lists.push_back(L);
   return (int)pj_lists.size() - 1;
 }

@@ -105,7 +105,9 @@ struct ApOut {
 struct ApList {
   int32_t out_begin, out_end;  // into the global ApOut table
   int32_t n_tiles;
-  double flops;  // algorithmic: 8 * P * d_leg per non-identity term and output
+  int32_t k = 1;       // CTAs sharing one output tile (thread-block cluster size, 1..8)
+  int32_t useful = 1;  // largest split that still gives every warp work
+  double flops;        // algorithmic: 8 * P * d_leg per non-identity term and output
 };
 // Projection job: E[x',x] = sum_r conj(U[.. x' at leg ..]) W[.. x at leg ..].
 struct PjOut {
@@ -118,7 +120,9 @@ struct PjOut {
 struct PjList {
   int32_t out_begin, out_end;
   int32_t n_tiles;
-  double flops;  // 8 * P * d_leg per output
+  int32_t k = 1;       // CTAs sharing one output tile (thread-block cluster size, 1..8)
+  int32_t useful = 1;  // largest split that still gives every warp >= 4 positions
+  double flops;        // 8 * P * d_leg per output
 };
 
 // Buffer ids used by job lists. Node slots come first (0..n_nodes-1).
@@ -173,6 +177,8 @@ struct Plan {
   int64_t P_cap_max = 0, theta_cap = 0;
   int r_cap_max = 1;
   int cap_rank = 32;
+  int sm_count = 152;  // SMs of the device: sizes the per-tile CTA split of the job lists
+  int max_split = 8;   // upper bound of that split (ttn_params.max_split)
 
   // classes
   std::vector<std::vector<ClassId>> dir_classes;  // per directed bond id
@@ -214,12 +220,14 @@ struct Plan {
   int n_sub(double tau, double kappa) const;
   bool built_jobs = false;
   std::string build_jobs();
+  void set_split(int max_split);  // recompute the split of every job list
 
  private:
   std::string build_classes();
   int new_mat(int d);
   int add_list(const std::vector<ApOut>& outs, const std::vector<std::vector<ApTerm>>& terms);
   int add_pj_list(const std::vector<PjOut>& outs);
+  int split_factor(int tiles, int useful) const;
   void node_terms(int u, int src, int t_base, std::vector<ApTerm>& singles,
                   std::vector<std::array<int, 4>>& pairs) const;
   // operator terms on an arbitrary list of (node, leg) "virtual legs"
@@ -229,5 +237,8 @@ struct Plan {
 
 constexpr int kApTile = 32;   // output elements per CTA of the apply kernel
 constexpr int kPjTile = 32;   // output entries per CTA of the projection kernel
+constexpr int kApChunk = 4;   // leg positions per work unit of the apply kernel
+constexpr int kSplitWarps = 8;  // warps per CTA of the apply / projection kernels
+constexpr int kMaxSplit = 8;    // at most this many CTAs (one cluster) share an output tile
 
 }  // namespace ttn

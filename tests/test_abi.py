@@ -79,6 +79,27 @@ def test_rank_caps_and_substeps_match_oracle(lib, make):
     lib.ttn_destroy(h)
 
 
+def test_params_round_trip_and_range_checks(lib):
+    from paper_2603_17711_gb300 import _lib, heom
+    w = W.spin_boson_tt()
+    st, h = _create(lib, w)
+    assert st == 0
+    p = _lib.ttn_params()
+    assert lib.ttn_get_params(h, C.byref(p)) == 0
+    assert (p.qr_tol, p.kappa, p.max_rank, p.max_split) == (1e-12, 2.5, 32, 8)
+    for field, bad in (("max_split", 0), ("max_split", 9), ("kappa", 0.0), ("ps2_ratio", 0.5), ("max_rank", 0)):
+        q = _lib.ttn_params()
+        C.memmove(C.byref(q), C.byref(p), C.sizeof(p))
+        setattr(q, field, bad)
+        assert lib.ttn_set_params(h, C.byref(q)) == 1, field  # TTN_EINVAL
+    p.max_split = 1
+    assert lib.ttn_set_params(h, C.byref(p)) == 0
+    assert _load(lib, h, heom.heom_sop(w.H, w.baths, w.depth)) == 0
+    q = _lib.ttn_params()
+    assert lib.ttn_get_params(h, C.byref(q)) == 0 and q.max_split == 1
+    lib.ttn_destroy(h)
+
+
 def test_invalid_trees_and_operators_are_rejected(lib):
     from paper_2603_17711_gb300 import heom
     w = W.spin_boson_tt(depth=4, n_pade=2)
