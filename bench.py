@@ -234,6 +234,38 @@ def bench_ours(args, rank, world, local_rank):
     ga.close()
     gb.close()
 
+    # ---- precision workload: the same chain at bond rank 64 (QRs up to 4096 x 64) ----
+    r64 = None
+    if not args.no_rank64:
+        w64 = W.exciton_chain(rank=64)
+        k64 = max(2, min(args.steps, 5))
+        res = {}
+        rhos = {}
+        for label, prec in (("fp64", 0), ("mixed_fp32", pkg.TTN_MIXED_FP32)):
+            gg = make_gpu(pkg, w64, local_rank, precision=prec)
+            gg.ttn_step(w64.dt, 1, 1)  # warm-up (graph capture)
+            torch.cuda.synchronize()
+            gg.ttn_stats_reset()
+            ms64 = timed_steps(torch, gg, w64, k64, flush)
+            fl64 = gg.ttn_stats(0)[1]
+            gg.ttn_stats_reset()
+            gg.ttn_profile(True)
+            timed_steps(torch, gg, w64, 1, flush)
+            gg.ttn_profile(False)
+            pr = {k: (gg.ttn_stats(k)[1], gg.ttn_profile_read(k)) for k in range(4)}
+            rhos[label] = gg.ttn_rdm()
+            res[label] = {"steps_per_s": k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64,
+                          "node_contraction_gflop_per_step": fl64 / k64 / 1e9,
+                          "node_contraction_tflops_kernel": pr[0][0] / (pr[0][1] * 1e-3) / 1e12 if pr[0][1] > 0 else None,
+                          "kernel_ms_per_step": {n_: pr[k][1] for k, n_ in
+                                                 enumerate(("k_apply", "environment", "qr", "other"))}}
+            gg.close()
+        r64 = {"workload": "7-site exciton chain as above at bond rank 64 (state 1.97 M complex, nodes 64x64x64)",
+               "steps_timed": k64, **res,
+               "mixed_speedup_vs_fp64": res["fp64"]["ms_per_step"] / res["mixed_fp32"]["ms_per_step"],
+               "rdm_max_abs_mixed_vs_fp64_gpu": float(np.max(np.abs(rhos["fp64"] - rhos["mixed_fp32"]))),
+               "steps_compared": 1 + k64 + 1}
+
     # ---- batched: 256 uneven spin-boson instances in one graph launch per step ----
     batch_out = None
     if not args.no_batch:
@@ -325,6 +357,7 @@ def bench_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 16 * w.M * w.M,
                 "includes": "handle build, sop_load, workspace bind, rho0 upload, K steps with rho_S read back each step"},
         "batched": batch_out,
+        "precision_rank64": r64,
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "wall_s_timed_region": wall,
@@ -373,6 +406,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-rank64", action="store_true", help="skip the rank-64 precision leg")
     ap.add_argument("--batch", type=int, default=256, help="instances in the batched leg")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

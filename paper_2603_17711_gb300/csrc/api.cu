@@ -51,6 +51,7 @@ struct ttn_ctx {
   double2* pool = nullptr;
   int prec = PREC_F64;
   double2* qr_work = nullptr;
+  int64_t qr_elems = 0;
   // ps2 scratch
   double2 *svd_A = nullptr, *svd_V = nullptr, *svd_Z = nullptr, *svd_Zg = nullptr, *svd_C = nullptr;
   double* svd_sigma = nullptr;
@@ -201,7 +202,15 @@ Layout layout_of(const Plan& p, int prec) {
   const int64_t nP = (int64_t)(4 + p.buf.n_t + p.buf.n_w) * S;
   L.scratch_elems = nP + 4 * r2 + 4 * p.theta_cap + 5 * p.theta_cap;
   L.scratch = take(L.scratch_elems * sizeof(double2));
+  // QR scratch: the one-CTA kernel needs S; the blocked path for tall
+  // matricisations (m x n, m*n <= S, n <= r_cap_max) needs its own layout
   L.qr_elems = S;
+  for (int u = 0; u < n; ++u)
+    for (int l = 0; l < 3; ++l) {
+      const int64_t nn = p.cap_dims[u][l];
+      if (nn < 1 || nn > kQrClusterMaxN) continue;
+      L.qr_elems = std::max<int64_t>(L.qr_elems, qr_blocked_elems(p.P_cap[u] / nn, nn));
+    }
   L.qr = take(L.qr_elems * sizeof(double2));
   L.rdm_off.resize(n);
   int64_t ra = 0;
@@ -284,7 +293,7 @@ struct Exec {
     // Householder factorisation + explicit Q: 2 (2 m n^2 - 2 n^3 / 3) complex MACs
     const double flops = 8.0 * 2.0 * (2.0 * m * n * n - 2.0 * n * n * n / 3.0);
     run(2, flops, [&] {
-      launch_qr(h->h_bufs[u], d[0], d[1], d[2], li, h->params.qr_tol, h->qr_work,
+      launch_qr(h->h_bufs[u], d[0], d[1], d[2], li, h->params.qr_tol, h->qr_work, h->qr_elems,
                 h->h_bufs[p.buf.tmp], h->h_bufs[p.buf.bond_y], h->flag_dev, lo_copy(u), lo_copy(p.buf.bond_y), s);
     });
   }
@@ -445,7 +454,7 @@ struct Exec {
         run(3, 0.0, [&] { launch_gauss(h->rs_omega, (int64_t)n * kk, 0x5eedull + 7919ull * h->n_splits, s); });
         run(2, 8.0 * m * n * kk, [&] { launch_zgemm(h->h_bufs[tl], h->rs_omega, h->rs_Y, m, kk, n, false, s); });
         run(2, 0.0, [&] {
-          launch_qr(h->rs_Y, m, 1, kk, 2, h->params.qr_tol, h->qr_work, h->h_bufs[p.buf.tmp], h->svd_V, h->flag_dev,
+          launch_qr(h->rs_Y, m, 1, kk, 2, h->params.qr_tol, h->qr_work, h->qr_elems, h->h_bufs[p.buf.tmp], h->svd_V, h->flag_dev,
                     nullptr, nullptr, s);
         });
         run(2, 8.0 * m * n * kk, [&] { launch_zgemm(h->rs_Y, h->h_bufs[tl], h->rs_B, kk, n, m, true, s); });
@@ -527,7 +536,7 @@ struct Exec {
     }
     if (g < r) {  // deterministic completion of the undetermined directions (Householder, tol 0)
       run(2, 0.0, [&] {
-        launch_qr(h->svd_Z, rows_iso, 1, r, 2, 0.0, h->qr_work, h->h_bufs[p.buf.tmp], h->svd_V, h->flag_dev,
+        launch_qr(h->svd_Z, rows_iso, 1, r, 2, 0.0, h->qr_work, h->qr_elems, h->h_bufs[p.buf.tmp], h->svd_V, h->flag_dev,
                   nullptr, nullptr, s);
       });
       run(3, 0.0, [&] { launch_restore_cols(h->svd_Z, h->svd_Zg, rows_iso, r, g, s); });
@@ -896,6 +905,7 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
       h->h_mats[i] = p.mats[i].off >= 0 ? h->pool + p.mats[i].off : nullptr;
     h->h_mats[p.bond_mat] = h->h_bufs[p.buf.bond_y];
     h->qr_work = (double2*)(base + L.qr);
+    h->qr_elems = L.qr_elems;
     h->rdm_vec = (double2*)(base + L.rdm);
     h->rdm_off = L.rdm_off;
     h->rho_dev = (double2*)(base + L.rho);

@@ -56,13 +56,40 @@ void launch_project(int prec, const DevTables& T, const PjList& L, cudaStream_t 
 // U is overwritten with Q (same layout), R (d_leg x d_leg, row-major) written to R.
 // work: >= P complex, qbuf: >= P complex. A non-finite ||U||_F sets *flag and
 // leaves U unchanged. U_lo / R_lo (nullable) receive FP32 copies of Q and R.
-void launch_qr(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work,
+// work_elems: capacity of work (the blocked path for tall matrices needs
+// qr_blocked_elems(m, n) of it; otherwise P suffices).
+void launch_qr(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work, int64_t work_elems,
                double2* qbuf, double2* R, int* flag, float2* U_lo, float2* R_lo, cudaStream_t s);
 // Cluster-parallel variant (qr.cu); returns false when the shape does not fit
 // (bond dim > kQrClusterMaxN or the row blocks exceed shared memory).
 constexpr int kQrClusterMaxN = 64;
 bool launch_qr_cluster(double2* U, int d0, int d1, int d2, int leg, double tol, double2* R, int* flag,
                        float2* U_lo, float2* R_lo, cudaStream_t s);
+// Panel of the blocked QR (qr_blocked.cu): the cluster kernel factors columns
+// [c0, c0+nb) of the column-major m x n matrix A over rows [c0, m) with the
+// threshold *thr of the whole matrix (NaN: do nothing), writes V / R entries
+// back in place, beta/alpha/phase/skip of those columns at index c0.., and the
+// panel's WY factor T (nb x nb, row-major) with H_c0..H_{c0+nb-1} = I - V T V^H.
+struct QrPanel {
+  double2* A;
+  int m, n, c0, nb;
+  const double* thr;
+  double* beta;
+  double* alpha;
+  double2* phase;
+  int* skip;
+  double2* T;
+};
+constexpr int kQrPanelMaxNb = 8;
+bool launch_qr_panel(const QrPanel& pn, cudaStream_t s);
+int qr_panel_cluster(int m_act, int nb);  // cluster size of a panel, 0 if it does not fit
+// Blocked Householder QR for matrices the cluster kernel cannot hold; same
+// convention and result as launch_qr. work needs qr_blocked_elems(m, n)
+// complex values; returns false (nothing launched) when it does not apply.
+int64_t qr_blocked_elems(int64_t m, int64_t n);
+bool launch_qr_blocked(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work,
+                       int64_t work_elems, double2* qbuf, double2* R, int* flag, float2* U_lo, float2* R_lo,
+                       cudaStream_t s);
 // dst = src (FP64); dst_lo (nullable) = FP32 copy.
 void launch_copy(double2* dst, float2* dst_lo, const double2* src, int64_t n, cudaStream_t s);
 // rho / vector contraction for one node: out[a] (non-root) or out[i*d1+j] (root)

@@ -45,10 +45,13 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kNW = kThreads / 32;
-constexpr int kG = 8;                      // lanes per trailing-column group
-constexpr int kGPW = 32 / kG;              // column groups per warp
-constexpr int kSlots = (kNW - 1) * kGPW;   // column groups of warps 1..7
-constexpr int kMaxPass = (kQrClusterMaxN - 1 + kSlots - 1) / kSlots;
+// G = lanes per trailing-column group (8 for whole small matrices, 32 for
+// panels of tall matrices, whose row blocks are long)
+template <int G> struct Grp {
+  static constexpr int kGPW = 32 / G;             // column groups per warp
+  static constexpr int kSlots = (kNW - 1) * kGPW;  // column groups of warps 1..7
+  static constexpr int kMaxPass = (kQrClusterMaxN - 1 + kSlots - 1) / kSlots;
+};
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ double2 cfmaj(double2 a, double2 b, double2 c) {  // conj(a)*b + c
@@ -69,9 +72,10 @@ __device__ __forceinline__ double wsum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
 }
-// sum over aligned groups of kG lanes; every lane of a group gets the same bits
+// sum over aligned groups of G lanes; every lane of a group gets the same bits
+template <int G>
 __device__ __forceinline__ double2 gsum2(double2 v) {
-  for (int o = kG / 2; o > 0; o >>= 1) {
+  for (int o = G / 2; o > 0; o >>= 1) {
     v.x += __shfl_xor_sync(kFull, v.x, o);
     v.y += __shfl_xor_sync(kFull, v.y, o);
   }
@@ -149,17 +153,23 @@ __device__ __forceinline__ void push_c64(uint32_t raddr, double2 v, uint32_t rmb
 //   G   [n][n]      partial strictly-upper Gram of my rows, later the gathered M
 //   GF  [n][n]      full strictly-upper Gram
 //   MM  [n][n]      the columns of M solved by this CTA
+template <int GL>
 __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int d1, int d2, int leg,
                                                          double tol, double2* R, int* flag, float2* U_lo,
-                                                         float2* R_lo) {
+                                                         float2* R_lo, QrPanel pn) {
+  using Gp = Grp<GL>;
+  constexpr int kGPW = Gp::kGPW, kSlots = Gp::kSlots, kMaxPass = Gp::kMaxPass;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int me = (int)cluster.block_rank();
   const int dd[3] = {d0, d1, d2};
   const int64_t st[3] = {(int64_t)d1 * d2, d2, 1};
-  const int n = dd[leg];
   const int la = leg == 0 ? 1 : 0, lb = leg == 2 ? 1 : 2;
-  const int m = dd[la] * dd[lb];
+  // panel mode: factor columns [c0, c0+nb) of the column-major m x n matrix
+  // pn.A over rows [c0, m) -- an (m - c0) x nb matrix in its own right
+  const bool panel = pn.A != nullptr;
+  const int n = panel ? pn.nb : dd[leg];
+  const int m = panel ? pn.m - pn.c0 : dd[la] * dd[lb];
   const int rp = (m + C - 1) / C;
   const int r0 = me * rp;
   const int nr = max(0, min(m, r0 + rp) - r0);
@@ -189,14 +199,15 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
 
-  // gather my rows: A[c][i] = U[.. row r0+i, column c ..]
+  // gather my rows: A[c][i] = U[.. row r0+i, column c ..] (panel: pn.A[c0+c][c0+r0+i])
   double fro = 0.0;
   for (int k = tid; k < n * rp; k += nt) {
     const int c = k / rp, i = k % rp;
     double2 v = make_double2(0.0, 0.0);
     if (i < nr) {
       const int r = r0 + i;
-      v = U[c * st[leg] + (int64_t)(r / dd[lb]) * st[la] + (int64_t)(r % dd[lb]) * st[lb]];
+      v = panel ? pn.A[(int64_t)(pn.c0 + c) * pn.m + pn.c0 + r]
+                : U[c * st[leg] + (int64_t)(r / dd[lb]) * st[la] + (int64_t)(r % dd[lb]) * st[lb]];
     }
     A[k] = v;
     fro = fma(v.x, v.x, fma(v.y, v.y, fro));
@@ -210,13 +221,14 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
     if (lane == 0) s_frob = sqrt(v);
   }
   __syncthreads();
-  const double frob = s_frob;
+  // the threshold of a panel is the one of the whole matrix (NaN: abort)
+  const double frob = panel ? *pn.thr : s_frob;
   if (!isfinite(frob)) {  // uniform across the cluster
-    if (tid == 0 && me == 0) atomicOr(flag, 1);
+    if (tid == 0 && me == 0 && !panel) atomicOr(flag, 1);
     cluster.sync();
     return;
   }
-  const double thr = tol * frob;  // s_part stays untouched until the final cluster barrier
+  const double thr = panel ? frob : tol * frob;  // s_part stays untouched until the final cluster barrier
   bool alive = true;
 
   // Partials of step j over my rows >= j, pushed into every CTA's slots of
@@ -242,19 +254,19 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
         if (own) push_c64(mapa(smem_u32(&SX[p]), lane), x[lrow], rmb);
       }
     } else {
-      const int q = (wid - 1) * kGPW + (lane >> 3), sl = lane & (kG - 1);
+      const int q = (wid - 1) * kGPW + lane / GL, sl = lane % GL;
       for (int kb = j + 1; kb < n; kb += kSlots) {  // block-uniform trip count
         const int k = kb + q;
         const double2* a = A + (size_t)min(k, n - 1) * rp;
         double2 u = make_double2(0.0, 0.0);
         if (k < n)
-          for (int i = i0 + sl; i < nr; i += kG) u = cfmaj(x[i], a[i], u);
-        u = gsum2(u);
+          for (int i = i0 + sl; i < nr; i += GL) u = cfmaj(x[i], a[i], u);
+        u = gsum2<GL>(u);
         if (alive && k < n) {
           const uint32_t su = smem_u32(&SU[((size_t)p * 16 + me) * n + k]);
           const uint32_t rj = smem_u32(&RJ[(size_t)p * n + k]);
           const uint32_t lmb = smem_u32(&mb[p]);
-          for (int c = sl; c < C; c += kG) {
+          for (int c = sl; c < C; c += GL) {
             const uint32_t rmb = mapa(lmb, c);
             push_c64(mapa(su, c), u, rmb);
             if (own) push_c64(mapa(rj, c), a[lrow], rmb);
@@ -312,26 +324,26 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
         }
       }
     } else {
-      const int q = (wid - 1) * kGPW + (lane >> 3), sl = lane & (kG - 1);
+      const int q = (wid - 1) * kGPW + lane / GL, sl = lane % GL;
 #pragma unroll
       for (int ps = 0; ps < kMaxPass; ++ps) {
         const int k = j + 1 + ps * kSlots + q;
         if (j + 1 + ps * kSlots >= n) break;  // block-uniform
         double2 w = make_double2(0.0, 0.0);
         if (k < n)
-          for (int c = sl; c < C; c += kG) {
+          for (int c = sl; c < C; c += GL) {
             const double2 t = SU[((size_t)p * 16 + c) * n + k];
             w.x += t.x;
             w.y += t.y;
           }
-        W[ps] = gsum2(w);
+        W[ps] = gsum2<GL>(w);
       }
     }
     __syncthreads();
     if (wid > 0 && !s_skip[j]) {
       const double beta = s_beta[j];
       const double2 gam = s_gam;
-      const int q = (wid - 1) * kGPW + (lane >> 3), sl = lane & (kG - 1);
+      const int q = (wid - 1) * kGPW + lane / GL, sl = lane % GL;
 #pragma unroll
       for (int ps = 0; ps < kMaxPass; ++ps) {
         const int k = j + 1 + ps * kSlots + q;
@@ -343,7 +355,7 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
           w.y = fma(gam.x, rj.y, fma(gam.y, rj.x, w.y));
           const double2 bw = make_double2(beta * w.x, beta * w.y);
           double2* a = A + (size_t)k * rp;
-          for (int i = i0 + sl; i < nr; i += kG) a[i] = cfms(x[i], bw, a[i]);
+          for (int i = i0 + sl; i < nr; i += GL) a[i] = cfms(x[i], bw, a[i]);
         }
       }
     }
@@ -351,9 +363,26 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
     if (j + 1 < n) push_partials(j + 1);
   }
   cluster.sync();  // all reflectors final everywhere, every pushed slot consumed
+  if (panel) {
+    // write the panel back (v below the diagonal, R entries above), the
+    // per-column scalars, and the WY factor T of the panel:
+    // T^{-1} = diag(1/beta) + strictly-upper(V^H V), column c of T solved by
+    // back substitution from e_c (skipped reflectors give zero rows/columns)
+    for (int k = tid; k < n * nr; k += nt) {
+      const int c = k / nr, i = k % nr;
+      pn.A[(int64_t)(pn.c0 + c) * pn.m + pn.c0 + r0 + i] = A[(size_t)c * rp + i];
+    }
+    if (me == 0)
+      for (int c = tid; c < n; c += nt) {
+        pn.beta[pn.c0 + c] = s_beta[c];
+        pn.alpha[pn.c0 + c] = s_alpha[c];
+        pn.phase[pn.c0 + c] = s_phase[c];
+        pn.skip[pn.c0 + c] = s_skip[c];
+      }
+  }
 
   // R rows owned here (global rows < n), diag(R) = alpha >= 0 after the phase fix
-  for (int k = tid; k < n * n; k += nt) {
+  for (int k = tid; !panel && k < n * n; k += nt) {
     const int i = k / n, c = k % n;
     if (i < r0 || i >= r0 + nr) continue;
     double2 v = make_double2(0.0, 0.0);
@@ -402,6 +431,24 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
     GF[a * n + b] = g;
   }
   __syncthreads();
+  if (panel) {
+    for (int c = me + C * wid; c < n; c += C * kNW) {
+      double2 acc0 = make_double2(lane == c ? 1.0 : 0.0, 0.0), acc1 = make_double2(lane + 32 == c ? 1.0 : 0.0, 0.0);
+      for (int a = c; a >= 0; --a) {
+        const double ba = s_beta[a];
+        const double2 src = a < 32 ? acc0 : acc1;
+        double2 ta = make_double2(ba * src.x, ba * src.y);
+        ta.x = __shfl_sync(kFull, ta.x, a & 31);
+        ta.y = __shfl_sync(kFull, ta.y, a & 31);
+        if (lane == (a & 31)) pn.T[a * n + c] = ta;
+        if (lane < a) acc0 = cfms(GF[lane * n + a], ta, acc0);
+        if (a > 32 && lane + 32 < a) acc1 = cfms(GF[(lane + 32) * n + a], ta, acc1);
+      }
+      for (int a = c + 1 + lane; a < n; a += 32) pn.T[a * n + c] = make_double2(0.0, 0.0);
+    }
+    cluster.sync();  // keep shared memory alive until every remote read has finished
+    return;
+  }
   // M = T V_top^H column by column: T^{-1} M[:, c] = conj(V_top[c, :])^T, with
   // T^{-1} = diag(1/beta) + strictly-upper Gram; back substitution from a = c
   // down (M[a][c] = 0 for a > c). Column c is solved by CTA c mod C, one warp.
@@ -468,17 +515,13 @@ int qr_cluster_size(int m, int n) {
   return C;
 }
 
-bool launch_qr_cluster(double2* U, int d0, int d1, int d2, int leg, double tol, double2* R, int* flag,
-                       float2* U_lo, float2* R_lo, cudaStream_t s) {
-  const int dd[3] = {d0, d1, d2};
-  const int n = dd[leg];
-  const int m = (int)((int64_t)d0 * d1 * d2 / n);
-  const int C = qr_cluster_size(m, n);
-  if (C == 0) return false;
+template <int G>
+static bool launch_cluster(double2* U, int d0, int d1, int d2, int leg, double tol, double2* R, int* flag,
+                           float2* U_lo, float2* R_lo, const QrPanel& pn, int m, int n, int C, cudaStream_t s) {
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(k_qr_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(k_qr_cluster<G>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_qr_cluster<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     attr_done = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -493,7 +536,31 @@ bool launch_qr_cluster(double2* U, int d0, int d1, int d2, int leg, double tol, 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_qr_cluster, U, d0, d1, d2, leg, tol, R, flag, U_lo, R_lo) == cudaSuccess;
+  return cudaLaunchKernelEx(&cfg, k_qr_cluster<G>, U, d0, d1, d2, leg, tol, R, flag, U_lo, R_lo, pn) == cudaSuccess;
+}
+
+bool launch_qr_cluster(double2* U, int d0, int d1, int d2, int leg, double tol, double2* R, int* flag,
+                       float2* U_lo, float2* R_lo, cudaStream_t s) {
+  const int dd[3] = {d0, d1, d2};
+  const int n = dd[leg];
+  const int m = (int)((int64_t)d0 * d1 * d2 / n);
+  const int C = qr_cluster_size(m, n);
+  if (C == 0) return false;
+  QrPanel pn = {};
+  return launch_cluster<8>(U, d0, d1, d2, leg, tol, R, flag, U_lo, R_lo, pn, m, n, C, s);
+}
+
+int qr_panel_cluster(int m_act, int nb) {
+  int C = (m_act + 7) / 8;
+  C = C < 1 ? 1 : (C > 16 ? 16 : C);
+  return qr_cluster_smem(m_act, nb, C) > 160 * 1024 ? 0 : C;
+}
+
+bool launch_qr_panel(const QrPanel& pn, cudaStream_t s) {
+  const int m_act = pn.m - pn.c0;
+  const int C = qr_panel_cluster(m_act, pn.nb);
+  if (C == 0 || pn.nb > kQrPanelMaxNb) return false;
+  return launch_cluster<32>(nullptr, 1, 1, 1, 0, 0.0, nullptr, nullptr, nullptr, nullptr, pn, m_act, pn.nb, C, s);
 }
 
 }  // namespace ttn
