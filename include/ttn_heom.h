@@ -92,7 +92,11 @@ typedef struct {
  *                    smaller than two CTAs per SM are split up to this factor
  *                    (no counterpart in the paper: GB300 work distribution).
  *                    Use 1 for instances advanced concurrently by
- *                    ttn_batch_step, which fill the GPU by themselves. */
+ *                    ttn_batch_step, which fill the GPU by themselves.
+ *  tensor_cores (1)  mixed form only: run the mode products of large nodes
+ *                    (contracted legs <= 64, >= 16384 elements) on the
+ *                    tcgen05 tensor cores in 3xTF32 (hi/lo split, FP32
+ *                    accumulation); 0 keeps them on the FP32 CUDA cores. */
 typedef struct {
   double qr_tol;
   double kappa;
@@ -101,6 +105,7 @@ typedef struct {
   int32_t max_rank;
   double svd_tol;
   int32_t max_split;
+  int32_t tensor_cores;
 } ttn_params;
 
 /* Create a handle (Sec. 2.3, Eq. omega_tensor). leg_dims[n_legs]: leg

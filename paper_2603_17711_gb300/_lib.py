@@ -29,7 +29,7 @@ class ttn_tree(C.Structure):
 class ttn_params(C.Structure):
     _fields_ = [("qr_tol", C.c_double), ("kappa", C.c_double), ("ps2_atol", C.c_double),
                 ("ps2_ratio", C.c_double), ("max_rank", C.c_int32), ("svd_tol", C.c_double),
-                ("max_split", C.c_int32)]
+                ("max_split", C.c_int32), ("tensor_cores", C.c_int32)]
 
 
 DRIVE_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)

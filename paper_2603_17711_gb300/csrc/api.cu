@@ -32,7 +32,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct ttn_ctx {
   Plan plan;
   int precision = TTN_FP64;
-  ttn_params params{1e-12, 2.5, 1e-7, 2.0, 32, 1e-12, kMaxSplit};
+  ttn_params params{1e-12, 2.5, 1e-7, 2.0, 32, 1e-12, kMaxSplit, 1};
   bool sop_loaded = false;
   bool ws_bound = false;
   bool envs_dirty = true;
@@ -52,6 +52,7 @@ struct ttn_ctx {
   int prec = PREC_F64;
   double2* qr_work = nullptr;
   int64_t qr_elems = 0;
+  float2* tc_acc = nullptr;  // FP32 scratch of the tensor-core path (mixed form)
   // ps2 scratch
   double2 *svd_A = nullptr, *svd_V = nullptr, *svd_Z = nullptr, *svd_Zg = nullptr, *svd_C = nullptr;
   double* svd_sigma = nullptr;
@@ -173,7 +174,7 @@ ttn_status cuda_fail(ttn_t h, cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 struct Layout {
   size_t nodes, pool, scratch, qr, rdm, rho, bufs_tab, mats_tab, terms, outs, pjs, drives, flag, total;
-  size_t nodes32 = 0, pool32 = 0, scratch32 = 0, bufs_tab_lo = 0, mats_tab_lo = 0;  // FP32 mode only
+  size_t nodes32 = 0, pool32 = 0, scratch32 = 0, bufs_tab_lo = 0, mats_tab_lo = 0, tc_acc = 0;  // FP32 mode only
   size_t svd_small = 0, rsvd = 0, mlp = 0;
   std::vector<int64_t> node_off;  // complex elements from `nodes`
   std::vector<int64_t> rdm_off;
@@ -237,6 +238,7 @@ Layout layout_of(const Plan& p, int prec) {
     // ys, T_g, W_c and the bond shadow / stage input in FP32
     L.scratch32 = take(((int64_t)(2 + p.buf.n_t + p.buf.n_w) * S + 3 * r2 + 3 * p.theta_cap) * sizeof(float2));
     L.bufs_tab_lo = take(p.buf.n_bufs * sizeof(void*));
+    L.tc_acc = take(S * sizeof(float2));
     L.mats_tab_lo = take(p.mats.size() * sizeof(void*));
   }
   L.total = off;
@@ -272,6 +274,14 @@ struct Exec {
   void apply(int kind, int list, const Epi& e) {
     if (list < 0) return;
     const ApList& L = p.ap_lists[list];
+    if (h->prec == PREC_F32 && h->params.tensor_cores && h->tc_acc &&
+        tc_applicable(L, p.ap_outs.data(), p.ap_terms.data())) {
+      run(kind, L.flops, [&] {
+        if (!launch_apply_tc(h->Tlo, L, e, p.ap_outs.data(), p.ap_terms.data(), h->tc_acc, h->flag_dev, s))
+          launch_apply(h->prec, h->Tlo, L, e, s);
+      });
+      return;
+    }
     run(kind, L.flops, [&] { launch_apply(h->prec, h->Tlo, L, e, s); });
   }
   void store(int kind, int list) { apply(kind, list, Epi{EPI_STORE, nullptr, nullptr, nullptr, nullptr, 0.0}); }
@@ -758,7 +768,8 @@ ttn_status ttn_set_params(ttn_t h, const ttn_params* prm) {
   return guarded(h, [&]() -> ttn_status {
     if (!prm) return h->fail(TTN_EINVAL, "null params");
     if (!(prm->qr_tol >= 0) || !(prm->kappa > 0) || !(prm->ps2_atol >= 0) || !(prm->ps2_ratio >= 1) ||
-        prm->max_rank < 1 || !(prm->svd_tol >= 0) || prm->max_split < 1 || prm->max_split > kMaxSplit)
+        prm->max_rank < 1 || !(prm->svd_tol >= 0) || prm->max_split < 1 || prm->max_split > kMaxSplit ||
+        (prm->tensor_cores != 0 && prm->tensor_cores != 1))
       return h->fail(TTN_EINVAL, "parameter out of range");
     if (h->ws_bound && prm->max_rank != h->params.max_rank)
       return h->fail(TTN_ESTATE, "max_rank must be set before the workspace is bound");
@@ -948,6 +959,7 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
       for (size_t i = 0; i < p.mats.size(); ++i)
         h->h_mats_lo[i] = p.mats[i].off >= 0 ? (void*)(p32 + p.mats[i].off) : nullptr;
       h->h_mats_lo[p.bond_mat] = h->h_bufs_lo[p.buf.bond_y];
+      h->tc_acc = (float2*)(base + L.tc_acc);
       h->Tlo.bufs = (void* const*)(base + L.bufs_tab_lo);
       h->Tlo.mats = (void* const*)(base + L.mats_tab_lo);
     }
@@ -1088,6 +1100,7 @@ static ttn_status check_flag(ttn_t h) {
   CUDA_TRY(h, cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   if (flag & 2) return h->fail(TTN_ETIMEOUT, "a cluster exchange of the QR kernel gave up after 2 s");
+  if (flag & 8) return h->fail(TTN_ETIMEOUT, "a tensor-core MMA wait gave up after 1 s");
   if (flag) return h->fail(TTN_ENUMERIC, "non-finite amplitude in the root tensor");
   return TTN_OK;
 }

@@ -51,6 +51,14 @@ struct DriveArgs {
 };
 
 void launch_apply(int prec, const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s);
+// Mixed form: the same list with its mode products on the tcgen05 tensor
+// cores (tc_apply.cu, 3xTF32). outs_host/terms_host: host copies of the job
+// tables; acc: FP32 scratch of the largest output (RK epilogue lists); flag
+// bit 3 on a timed-out MMA wait. tc_applicable: 3-leg outputs, contracted
+// legs of dimension <= 64, largest output >= 16384 elements.
+bool tc_applicable(const ApList& L, const ApOut* outs_host, const ApTerm* terms_host);
+bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const ApOut* outs_host,
+                     const ApTerm* terms_host, float2* acc, int* flag, cudaStream_t s);
 void launch_project(int prec, const DevTables& T, const PjList& L, cudaStream_t s);
 // Householder QR of node tensor U (dims d[3]) matricised toward leg `leg`.
 // U is overwritten with Q (same layout), R (d_leg x d_leg, row-major) written to R.

@@ -1,0 +1,403 @@
+// Mode products of the mixed-precision form on the 5th-generation tensor cores
+// (tcgen05, kind::tf32, accumulator in tensor memory).
+//
+// One term Y += M x_l X (M complex d x d, d = d_l <= 64) is a real GEMM through
+// the 2x2 embedding of every complex entry,
+//     (Re Y, Im Y) = [[Re M, -Im M], [Im M, Re M]] . (Re X, Im X),
+// with real and imaginary parts interleaved along both the MMA's M dimension
+// (2d <= 128 rows, zero-padded) and K (2d, in chunks of 32); n, the positions
+// of the two other legs, is the N dimension (tiles of 64). All terms of an output on the same leg accumulate into one
+// tensor-memory tile; the legs are separate launches (0, 1, 2) so that the
+// first writes the output and the later ones add to it, in that fixed order.
+// Precision: every FP32 operand is split into tf32 hi + lo, and the three
+// products hi*hi + hi*lo + lo*hi are accumulated in FP32 ("3xTF32"), which
+// keeps the error at the level of FP32 CUDA-core arithmetic.
+//
+// Operands are staged by the threads (the 2x2 embedding and the hi/lo split
+// happen on the way) into shared memory in the K-major, unswizzled canonical
+// layout: 8-row x 16-byte core matrices, K-adjacent core matrices 128 B apart
+// (leading byte offset), 8-row groups 1024 B apart (stride byte offset). Two
+// stages alternate so that staging chunk c+1 overlaps the MMAs of chunk c;
+// one thread issues the MMAs and commits them to the stage's mbarrier.
+#include <algorithm>
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace ttn {
+
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kTcM = 128;  // MMA rows (2d, zero-padded)
+constexpr int kTcN = 64;   // positions per tile (MMA N)
+constexpr int kTcK = 32;   // K per staged chunk (4 MMAs of K = 8)
+constexpr int kAElems = kTcM * kTcK;  // floats per A chunk (hi or lo)
+constexpr int kBElems = kTcN * kTcK;
+constexpr int kStageFloats = 2 * kAElems + 2 * kBElems;
+constexpr size_t kTcSmem = 2 * kStageFloats * sizeof(float);  // 96 KB
+constexpr int64_t kTcMinElems = 16384;  // smaller lists stay on the CUDA cores
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// float offset of element (r, k) of an R x kTcK chunk in the canonical layout
+__device__ __forceinline__ int cm_off(int r, int k) { return ((r >> 3) * (kTcK / 4) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3); }
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)(128 >> 4) << 16;                  // leading byte offset: next core matrix along K
+  d |= (uint64_t)((kTcK / 4 * 128) >> 4) << 32;     // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                           // descriptor version; base offset 0, no swizzle
+  return d;
+}
+__device__ __forceinline__ float tf32_hi(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ bool mbar_done(uint64_t* mb, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok)
+               : "r"(smem_u32(mb)), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* mb, uint32_t parity, uint64_t deadline) {
+  while (!mbar_done(mb, parity))
+    if (gtimer() > deadline) return false;
+  return true;
+}
+
+struct Geo3 {
+  int d[3];
+  int64_t st[3];
+};
+__device__ __forceinline__ Geo3 geo_of(const ApOut& o) {
+  Geo3 g;
+  g.d[0] = o.d0;
+  g.d[1] = o.d1;
+  g.d[2] = o.d2;
+  g.st[0] = (int64_t)o.d1 * o.d2;
+  g.st[1] = o.d2;
+  g.st[2] = 1;
+  return g;
+}
+// Embedded operands interleave real and imaginary parts: row 2i + c of A is
+// component c of output index i, column 2x + c' pairs with component c' of X
+// at leg index x, so A[2i+c][2x+c'] = (Re M, -Im M; Im M, Re M)[c][c'] at
+// M[i][x] and B[n][2x+c'] = component c' of X at (x, position n). A chunk of
+// 32 K columns covers 16 leg indices x; each complex value is read once.
+// base[nn]: offset of tile position nn over the two other legs.
+__device__ void stage_chunk(float* buf, const float2* __restrict__ M, const float2* __restrict__ X, int d,
+                            int64_t st_l, bool x_fast, const int64_t* base, int nvalid, int kc) {
+  float* Ah = buf;
+  float* Al = buf + kAElems;
+  float* Bh = buf + 2 * kAElems;
+  float* Bl = Bh + kBElems;
+  const int x0 = kc * (kTcK / 2);
+  for (int e = threadIdx.x; e < (kTcM / 2) * (kTcK / 2); e += kTcThreads) {
+    const int i = e >> 4, xl = e & 15, x = x0 + xl;
+    const float2 m = (i < d && x < d) ? M[i * d + x] : make_float2(0.f, 0.f);
+    const float v[4] = {m.x, -m.y, m.y, m.x};  // (c, c') = (0,0), (0,1), (1,0), (1,1)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int o = cm_off(2 * i + (q >> 1), 2 * xl + (q & 1));
+      const float h = tf32_hi(v[q]);
+      Ah[o] = h;
+      Al[o] = tf32_hi(v[q] - h);
+    }
+  }
+  for (int e = threadIdx.x; e < kTcN * (kTcK / 2); e += kTcThreads) {
+    // consecutive threads walk the contiguous direction of X
+    const int nn = x_fast ? e >> 4 : e % kTcN, xl = x_fast ? e & 15 : e / kTcN, x = x0 + xl;
+    const float2 v = (nn < nvalid && x < d) ? X[(int64_t)x * st_l + base[nn]] : make_float2(0.f, 0.f);
+    const int o0 = cm_off(nn, 2 * xl), o1 = cm_off(nn, 2 * xl + 1);
+    const float h0 = tf32_hi(v.x), h1 = tf32_hi(v.y);
+    Bh[o0] = h0;
+    Bl[o0] = tf32_hi(v.x - h0);
+    Bh[o1] = h1;
+    Bl[o1] = tf32_hi(v.y - h1);
+  }
+}
+
+// One CTA = one (output, 64-position tile) of leg `leg`: Y_o (+)= sum over the
+// output's terms on this leg of M_t x_leg X_t. Y_o is the STORE destination
+// (or acc for an RK epilogue list); the first leg with terms writes, later
+// legs add. Flag bit 3 on a timed-out MMA wait.
+__global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, int leg, float2* acc, int* flag) {
+  extern __shared__ __align__(128) float tsm[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ int64_t base[kTcN];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // locate the output and tile of this CTA
+  int o = L.out_begin, tile = blockIdx.x;
+  int64_t rest = 0;
+  for (;; ++o) {
+    if (o >= L.out_end) return;
+    const ApOut& u = T.outs[o];
+    const int dl = leg == 0 ? u.d0 : leg == 1 ? u.d1 : u.d2;
+    rest = (int64_t)u.d0 * u.d1 * u.d2 / dl;
+    const int nt = (int)((rest + kTcN - 1) / kTcN);
+    if (tile < nt) break;
+    tile -= nt;
+  }
+  const ApOut out = T.outs[o];
+  const Geo3 g = geo_of(out);
+  int n_here = 0;
+  bool earlier = false;
+  for (int t = out.term_begin; t < out.term_end; ++t) {
+    const ApTerm tm = T.terms[t];
+    if (tm.mat < 0) continue;
+    if (tm.leg == leg) ++n_here;
+    if (tm.leg < leg) earlier = true;
+  }
+  if (n_here == 0) return;  // uniform over the CTA
+  const int d = g.d[leg];
+  const int nkc = (2 * d + kTcK - 1) / kTcK;
+  const int nchunks = n_here * nkc;
+  const int64_t n0 = (int64_t)tile * kTcN;
+  const int nvalid = rest - n0 < kTcN ? (int)(rest - n0) : kTcN;
+  {
+    const int la = leg == 0 ? 1 : 0, lb = leg == 2 ? 1 : 2;
+    for (int nn = tid; nn < kTcN; nn += kTcThreads) {
+      const int64_t n = n0 + nn;
+      base[nn] = (n / g.d[lb]) * g.st[la] + (n % g.d[lb]) * g.st[lb];
+    }
+  }
+  __syncthreads();
+  float2* Y = L.out_end - L.out_begin == 1 && acc ? acc : (float2*)T.bufs[out.dst];
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // instruction descriptor: D f32, A/B tf32, both K-major, N = 64, M = 128
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+  const uint64_t deadline = gtimer() + 1000000000ull;
+  bool ok = true;
+  uint32_t ph[2] = {0u, 0u};
+
+  // chunk ci -> (term, kc)
+  auto chunk_src = [&](int ci, const float2*& M, const float2*& X, int& kc) {
+    int k = ci / nkc;
+    kc = ci % nkc;
+    for (int t = out.term_begin; t < out.term_end; ++t) {
+      const ApTerm tm = T.terms[t];
+      if (tm.mat < 0 || tm.leg != leg) continue;
+      if (k-- == 0) {
+        M = (const float2*)T.mats[tm.mat];
+        X = (const float2*)T.bufs[tm.src];
+        return;
+      }
+    }
+  };
+  {
+    const float2 *M, *X;
+    int kc;
+    chunk_src(0, M, X, kc);
+    stage_chunk(tsm, M, X, d, g.st[leg], leg == 2, base, nvalid, kc);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  for (int ci = 0; ci < nchunks; ++ci) {
+    const int b = ci & 1;
+    float* buf = tsm + b * kStageFloats;
+    // make the staged operands visible to the tensor core, then issue
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0 && ok) {
+      const uint32_t ah = smem_u32(buf), al = ah + kAElems * 4, bh = al + kAElems * 4, bl = bh + kBElems * 4;
+      const uint32_t a_op[3] = {ah, ah, al}, b_op[3] = {bh, bl, bh};
+      for (int pass = 0; pass < 3; ++pass)
+        for (int ks = 0; ks < kTcK / 8; ++ks) {
+          const uint64_t ad = sdesc(a_op[pass] + ks * 256), bd = sdesc(b_op[pass] + ks * 256);
+          const uint32_t accum = (ci > 0 || pass > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+              : "memory");
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&mbar[b]))
+                   : "memory");
+    }
+    if (ci + 1 < nchunks) {
+      // the other stage is free once the MMAs of chunk ci-1 have completed
+      if (ci >= 1 && ok) {
+        ok = mbar_wait(&mbar[b ^ 1], ph[b ^ 1], deadline);
+        ph[b ^ 1] ^= 1u;
+      }
+      const float2 *M, *X;
+      int kc;
+      chunk_src(ci + 1, M, X, kc);
+      stage_chunk(tsm + (b ^ 1) * kStageFloats, M, X, d, g.st[leg], leg == 2, base, nvalid, kc);
+    }
+  }
+  // all MMAs done once the last commit has landed (they complete in order)
+  if (ok) ok = mbar_wait(&mbar[(nchunks - 1) & 1], ph[(nchunks - 1) & 1], deadline);
+  ok = __syncthreads_and(ok) != 0;  // CTA-uniform: tcgen05.ld below is warp-collective
+  if (!ok && tid == 0) atomicOr(flag, 8);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // tensor memory -> shared (rows = embedded output rows, 64 columns)
+  float* Ds = tsm;  // [128][65]
+  if (ok) {
+    const int q = warp & 3, h = warp >> 2;
+    uint32_t r[32];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int row = 32 * q + lane;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) Ds[row * 65 + 32 * h + j] = __uint_as_float(r[j]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+  if (!ok) return;
+  // write (or add) the complex outputs: Y(i, n) = Ds[2i][n] + i Ds[2i+1][n]
+  for (int e = tid; e < d * kTcN; e += kTcThreads) {
+    const int i = e / kTcN, nn = e % kTcN;
+    if (nn >= nvalid) continue;
+    const int64_t at = (int64_t)i * g.st[leg] + base[nn];
+    float2 v = make_float2(Ds[(2 * i) * 65 + nn], Ds[(2 * i + 1) * 65 + nn]);
+    if (earlier) {
+      const float2 y = Y[at];
+      v.x += y.x;
+      v.y += y.y;
+    }
+    Y[at] = v;
+  }
+}
+
+// Identity terms and the epilogue (RK4 stage update or nothing) of a list
+// whose mode products ran on the tensor cores: the tiles of the apply kernel
+// (32 elements), one thread per element.
+__global__ void k_tc_epilogue(DevTables T, ApList L, Epi ep, const float2* acc) {
+  const int tile = blockIdx.x;
+  int o = L.out_begin;
+  while (o + 1 < L.out_end && T.outs[o + 1].tile0 <= tile) ++o;
+  const ApOut out = T.outs[o];
+  const int64_t P = (int64_t)out.d0 * out.d1 * out.d2;
+  const int64_t e = (int64_t)(tile - out.tile0) * kApTile + threadIdx.x;
+  if (e >= P) return;
+  bool any = false;
+  float2 s = make_float2(0.f, 0.f);
+  for (int t = out.term_begin; t < out.term_end; ++t) {
+    const ApTerm tm = T.terms[t];
+    if (tm.mat >= 0) {
+      any = true;
+      continue;
+    }
+    const float2 v = ((const float2*)T.bufs[tm.src])[e];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  const bool rk = ep.mode != EPI_STORE;
+  float2* Y = rk ? const_cast<float2*>(acc) : (float2*)T.bufs[out.dst];
+  if (any) {
+    const float2 y = Y[e];
+    s.x += y.x;
+    s.y += y.y;
+  }
+  if (!rk) {
+    Y[e] = s;
+    return;
+  }
+  const double2 k = make_double2(s.x, s.y);
+  double2* y = ep.y;
+  double2* ac = ep.acc;
+  float2* ys = (float2*)ep.ys;
+  const double h = ep.h;
+  switch (ep.mode) {
+    case EPI_RK1:
+      ac[e] = k;
+      ys[e] = make_float2((float)(y[e].x + 0.5 * h * k.x), (float)(y[e].y + 0.5 * h * k.y));
+      break;
+    case EPI_RK2:
+      ac[e] = make_double2(ac[e].x + 2.0 * k.x, ac[e].y + 2.0 * k.y);
+      ys[e] = make_float2((float)(y[e].x + 0.5 * h * k.x), (float)(y[e].y + 0.5 * h * k.y));
+      break;
+    case EPI_RK3:
+      ac[e] = make_double2(ac[e].x + 2.0 * k.x, ac[e].y + 2.0 * k.y);
+      ys[e] = make_float2((float)(y[e].x + h * k.x), (float)(y[e].y + h * k.y));
+      break;
+    default: {
+      const double2 yn = make_double2(y[e].x + h / 6.0 * (ac[e].x + k.x), y[e].y + h / 6.0 * (ac[e].y + k.y));
+      y[e] = yn;
+      ((float2*)ep.y_lo)[e] = make_float2((float)yn.x, (float)yn.y);
+      break;
+    }
+  }
+}
+
+}  // namespace
+
+bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const ApOut* outs_host,
+                     const ApTerm* terms_host, float2* acc, int* flag, cudaStream_t s) {
+  if (L.n_tiles <= 0) return true;
+  const bool rk = e.mode != EPI_STORE;
+  if (rk && (L.out_end - L.out_begin != 1 || !acc)) return false;
+  int tiles[3] = {0, 0, 0};
+  bool has[3] = {false, false, false}, ident = false;
+  for (int o = L.out_begin; o < L.out_end; ++o) {
+    const ApOut& u = outs_host[o];
+    const int dd[3] = {u.d0, u.d1, u.d2};
+    for (int l = 0; l < 3; ++l) tiles[l] += (int)(((int64_t)u.d0 * u.d1 * u.d2 / dd[l] + kTcN - 1) / kTcN);
+    for (int t = u.term_begin; t < u.term_end; ++t) {
+      if (terms_host[t].mat < 0)
+        ident = true;
+      else
+        has[terms_host[t].leg] = true;
+    }
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    attr = true;
+  }
+  for (int l = 0; l < 3; ++l)
+    if (has[l]) k_tc_apply<<<tiles[l], kTcThreads, kTcSmem, s>>>(T, L, l, rk ? acc : nullptr, flag);
+  if (rk || ident) k_tc_epilogue<<<L.n_tiles, 32, 0, s>>>(T, L, e, acc);
+  return true;
+}
+
+bool tc_applicable(const ApList& L, const ApOut* outs_host, const ApTerm* terms_host) {
+  int64_t pmax = 0;
+  for (int o = L.out_begin; o < L.out_end; ++o) {
+    const ApOut& u = outs_host[o];
+    if (u.d3 != 1) return false;
+    const int dd[3] = {u.d0, u.d1, u.d2};
+    pmax = std::max<int64_t>(pmax, (int64_t)u.d0 * u.d1 * u.d2);
+    for (int t = u.term_begin; t < u.term_end; ++t) {
+      const ApTerm& tm = terms_host[t];
+      if (tm.mat < 0) continue;
+      if (tm.leg < 0 || tm.leg > 2 || dd[tm.leg] > kTcM / 2) return false;
+    }
+  }
+  return pmax >= kTcMinElems;
+}
+
+}  // namespace ttn

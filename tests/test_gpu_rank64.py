@@ -82,3 +82,26 @@ def test_rank64_seven_site_chain_mixed_vs_fp64(pkg):
     ga.close()
     gb.close()
     assert err <= 1e-6
+
+
+def test_rank64_tensor_cores_match_cuda_cores(pkg):
+    """The mixed form with its large mode products on the tcgen05 tensor cores
+    (3xTF32) against the same form on the FP32 CUDA cores and the oracle."""
+    w = W.exciton_chain(n_sites=3, depth=4, rank=64)
+    ga = gpu_from(pkg, w, precision=pkg.TTN_MIXED_FP32)
+    gb = gpu_from(pkg, w, precision=pkg.TTN_MIXED_FP32)
+    gb.ttn_set_params(tensor_cores=0)
+    o = ottn.from_workload(w)
+    e_tc = e_ref = diff = 0.0
+    for _ in range(3):
+        ga.ttn_step(w.dt, pkg.TTN_PS1, 1)
+        gb.ttn_step(w.dt, pkg.TTN_PS1, 1)
+        o.step(w.dt, "ps1")
+        ra, rb, ro = ga.ttn_rdm(), gb.ttn_rdm(), o.rdm()
+        e_tc = max(e_tc, float(np.max(np.abs(ra - ro))))
+        e_ref = max(e_ref, float(np.max(np.abs(rb - ro))))
+        diff = max(diff, float(np.max(np.abs(ra - rb))))
+    ga.close()
+    gb.close()
+    assert e_tc <= 1e-6 and e_ref <= 1e-6
+    assert diff <= 1e-6
