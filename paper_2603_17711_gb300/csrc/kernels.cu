@@ -3,6 +3,7 @@
 // On GB300 the FP64 pipe issues about 2 FMA per SM per clock, so every kernel
 // here is bound by FP64 issue, not by memory: the data (node tensors of at most
 // a few hundred KB, environments of r x r) stays in L2 and L1.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "kernels.cuh"
@@ -133,25 +134,25 @@ __device__ __forceinline__ typename Cx<R>::T unit_dot(const ApTerm& term, const 
   return acc;
 }
 
+// Sum of one output tile over the units of CTA `rank` of the k sharing it;
+// the CTA's total (fixed order over warps) is returned in warp 0.
 template <typename R>
-__global__ void __launch_bounds__(32 * kApWarps, 4) k_apply(DevTables T, ApList L, Epi ep) {
+__device__ __forceinline__ typename Cx<R>::T tile_sum(const DevTables& T, const ApList& L, int tile, int rank, int K,
+                                                      typename Cx<R>::T (*part)[32], ApOut& out, int64_t& idx,
+                                                      int64_t& P) {
   using C = Cx<R>;
   using V = typename C::T;
-  __shared__ V part[kApWarps][32];
-  __shared__ V slot[kMaxSplit][32];
-  const int K = L.k;
-  const int tile = blockIdx.x / K, rank = blockIdx.x % K;  // rank == block rank in the cluster
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int o = L.out_begin;
   while (o + 1 < L.out_end && T.outs[o + 1].tile0 <= tile) ++o;
-  const ApOut out = T.outs[o];
+  out = T.outs[o];
   Geo g;
   g.d0 = out.d0; g.d1 = out.d1; g.d2 = out.d2; g.d3 = out.d3;
   g.s2 = g.d3;
   g.s1 = (int64_t)g.d2 * g.d3;
   g.s0 = g.s1 * g.d1;
-  const int64_t P = g.s0 * g.d0;
-  const int64_t idx = (int64_t)(tile - out.tile0) * kApTile + lane;
+  P = g.s0 * g.d0;
+  idx = (int64_t)(tile - out.tile0) * kApTile + lane;
   V acc = C::zero();
   if (idx < P) {
     g.i0 = (int)(idx / g.s0);
@@ -174,15 +175,16 @@ __global__ void __launch_bounds__(32 * kApWarps, 4) k_apply(DevTables T, ApList 
     acc = part[0][lane];
     for (int w = 1; w < kApWarps; ++w) acc = C::add(acc, part[w][lane]);
   }
-  if (K > 1) {
-    cg::cluster_group cluster = cg::this_cluster();
-    if (wid == 0 && rank > 0) cluster.map_shared_rank(&slot[0][0], 0)[rank * 32 + lane] = acc;
-    cluster.sync();
-    if (rank > 0) return;
-    if (wid == 0)
-      for (int r = 1; r < K; ++r) acc = C::add(acc, slot[r][lane]);
-  }
-  if (wid != 0 || idx >= P) return;
+  __syncthreads();  // part may be reused by the caller's next tile
+  return acc;
+}
+
+// Epilogue of one output element (warp 0 of the CTA owning the tile).
+template <typename R>
+__device__ __forceinline__ void tile_store(const DevTables& T, const ApOut& out, const Epi& ep, int64_t idx,
+                                           typename Cx<R>::T acc) {
+  using C = Cx<R>;
+  using V = typename C::T;
   if (ep.mode == EPI_STORE) {
     ((V*)T.bufs[out.dst])[idx] = acc;
     return;
@@ -214,6 +216,70 @@ __global__ void __launch_bounds__(32 * kApWarps, 4) k_apply(DevTables T, ApList 
   }
 }
 
+template <typename R>
+__global__ void __launch_bounds__(32 * kApWarps, 4) k_apply(DevTables T, ApList L, Epi ep) {
+  using C = Cx<R>;
+  using V = typename C::T;
+  __shared__ V part[kApWarps][32];
+  __shared__ V slot[kMaxSplit][32];
+  const int K = L.k;
+  const int tile = blockIdx.x / K, rank = blockIdx.x % K;  // rank == block rank in the cluster
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  ApOut out;
+  int64_t idx, P;
+  V acc = tile_sum<R>(T, L, tile, rank, K, part, out, idx, P);
+  if (K > 1) {
+    cg::cluster_group cluster = cg::this_cluster();
+    if (wid == 0 && rank > 0) cluster.map_shared_rank(&slot[0][0], 0)[rank * 32 + lane] = acc;
+    cluster.sync();
+    if (rank > 0) return;
+    if (wid == 0)
+      for (int r = 1; r < K; ++r) acc = C::add(acc, slot[r][lane]);
+  }
+  if (wid != 0 || idx >= P) return;
+  tile_store<R>(T, out, ep, idx, acc);
+}
+
+// A whole RK4 flow (m substeps x 4 stages, each the pair first stage then the
+// combine with its epilogue) of a small tensor in ONE launch: one cluster of
+// C CTAs walks the tiles of each list; cluster barriers separate the phases
+// (a phase reads what the previous one wrote in other CTAs' tiles). Stage
+// inputs alternate as in the per-launch path: stage s reads var[s] and writes
+// the other buffer.
+template <typename R>
+__global__ void __launch_bounds__(32 * kApWarps) k_flow(DevTables T, FlowArgs F) {
+  using C = Cx<R>;
+  using V = typename C::T;
+  __shared__ V part[kApWarps][32];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int Cn = (int)cluster.num_blocks(), me = (int)cluster.block_rank();
+  const int wid = threadIdx.x >> 5;
+  const int src_var[5] = {0, 0, 1, 2, 1};
+  for (int sub = 0; sub < F.m; ++sub)
+    for (int st = 1; st <= 4; ++st) {
+      const int var = src_var[st];
+      if (F.first[var].n_tiles > 0) {
+        const ApList& L = F.first[var];
+        for (int tile = me; tile < L.n_tiles; tile += Cn) {
+          ApOut out;
+          int64_t idx, P;
+          const V acc = tile_sum<R>(T, L, tile, 0, 1, part, out, idx, P);
+          if (wid == 0 && idx < P) ((V*)T.bufs[out.dst])[idx] = acc;
+        }
+        cluster.sync();
+      }
+      const ApList& L = F.combine[var];
+      const Epi ep{st, F.y, F.y_lo, st == 2 ? F.ysB : F.ysA, F.acc, F.h};
+      for (int tile = me; tile < L.n_tiles; tile += Cn) {
+        ApOut out;
+        int64_t idx, P;
+        const V acc = tile_sum<R>(T, L, tile, 0, 1, part, out, idx, P);
+        if (wid == 0 && idx < P) tile_store<R>(T, out, ep, idx, acc);
+      }
+      cluster.sync();
+    }
+}
+
 // Launch n_tiles * k CTAs; k > 1 makes every k consecutive CTAs one cluster.
 template <typename Kern, typename... Args>
 static void launch_split(Kern kern, int n_tiles, int k, cudaStream_t s, Args... args) {
@@ -234,6 +300,33 @@ static void launch_split(Kern kern, int n_tiles, int k, cudaStream_t s, Args... 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+bool launch_flow(int prec, const DevTables& T, const FlowArgs& F, cudaStream_t s) {
+  int tiles = 0;
+  for (int v = 0; v < 3; ++v) tiles = std::max(tiles, std::max(F.first[v].n_tiles, F.combine[v].n_tiles));
+  if (tiles <= 0 || tiles > kFlowMaxTiles) return false;
+  const int C = std::min(tiles, 16);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_flow<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_flow<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)C, 1, 1);
+  cfg.blockDim = dim3(32 * kApWarps, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr1[1];
+  attr1[0].id = cudaLaunchAttributeClusterDimension;
+  attr1[0].val.clusterDim.x = (unsigned)C;
+  attr1[0].val.clusterDim.y = 1;
+  attr1[0].val.clusterDim.z = 1;
+  cfg.attrs = attr1;
+  cfg.numAttrs = 1;
+  if (prec == PREC_F32) return cudaLaunchKernelEx(&cfg, k_flow<float>, T, F) == cudaSuccess;
+  return cudaLaunchKernelEx(&cfg, k_flow<double>, T, F) == cudaSuccess;
 }
 
 void launch_apply(int prec, const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s) {

@@ -345,3 +345,22 @@ def test_ps2_then_ps1_mixed_strategy(pkg):
         err = max(err, float(np.max(np.abs(g.ttn_rdm() - o.rdm()))))
     g.close()
     assert err <= TOL_SHORT
+
+
+def test_ps2_and_ps1_runs_are_bitwise_repeatable(pkg):
+    """Three fresh handles on the same input give bit-identical trajectories
+    (fixed reduction orders everywhere; a race or an unsynchronised host read
+    would show up here first)."""
+    for scheme, w in (("ps2", W.spin_boson_tt(depth=4, n_pade=3, rank=3, tree="btt")),
+                      ("ps1", W.exciton_chain(n_sites=3, rank=7, depth=4))):
+        code = pkg.TTN_PS1 if scheme == "ps1" else pkg.TTN_PS2
+        runs = []
+        for _ in range(3):
+            g = gpu_from(pkg, w, params={"max_rank": 8, "ps2_atol": 1e-7})
+            traj = []
+            for _ in range(8):
+                g.ttn_step(w.dt, code, 1)
+                traj.append(g.ttn_rdm())
+            runs.append(np.array(traj))
+            g.close()
+        assert np.array_equal(runs[0], runs[1]) and np.array_equal(runs[0], runs[2]), scheme
