@@ -324,33 +324,6 @@ struct Exec {
   void rk4(const FlowLists& F, int y, int ysA, int ysB, int acc, double tau) {
     const int m = p.n_sub(tau, h->params.kappa);
     const double hs = tau / m;
-    // small flows (every list <= kFlowMaxTiles tiles): all stages in one cluster launch
-    if (F.combine[0] >= 0 && F.combine[1] >= 0 && F.combine[2] >= 0) {
-      FlowArgs fa{};
-      double flops = 0.0;
-      int tiles = 0;
-      static const int var_of[5] = {0, 0, 1, 2, 1};
-      for (int v = 0; v < 3; ++v) {
-        fa.first[v] = F.first[v] >= 0 ? p.ap_lists[F.first[v]] : ApList{};
-        if (F.first[v] < 0) fa.first[v].n_tiles = 0;
-        fa.combine[v] = p.ap_lists[F.combine[v]];
-        tiles = std::max(tiles, std::max(fa.first[v].n_tiles, fa.combine[v].n_tiles));
-      }
-      for (int st = 1; st <= 4; ++st)
-        flops += m * ((F.first[var_of[st]] >= 0 ? fa.first[var_of[st]].flops : 0.0) + fa.combine[var_of[st]].flops);
-      if (tiles <= kFlowMaxTiles) {
-        fa.y = h->h_bufs[y];
-        fa.y_lo = h->h_bufs_lo[y];
-        fa.ysA = h->h_bufs_lo[ysA];
-        fa.ysB = h->h_bufs_lo[ysB];
-        fa.acc = h->h_bufs[acc];
-        fa.h = hs;
-        fa.m = m;
-        bool ok = false;
-        run(0, flops, [&] { ok = launch_flow(h->prec, h->Tlo, fa, s); });
-        if (ok) return;
-      }
-    }
     static const int src_var[5] = {0, 0, 1, 2, 1};
     for (int sub = 0; sub < m; ++sub)
       for (int st = 1; st <= 4; ++st) {

@@ -240,46 +240,6 @@ __global__ void __launch_bounds__(32 * kApWarps, 4) k_apply(DevTables T, ApList 
   tile_store<R>(T, out, ep, idx, acc);
 }
 
-// A whole RK4 flow (m substeps x 4 stages, each the pair first stage then the
-// combine with its epilogue) of a small tensor in ONE launch: one cluster of
-// C CTAs walks the tiles of each list; cluster barriers separate the phases
-// (a phase reads what the previous one wrote in other CTAs' tiles). Stage
-// inputs alternate as in the per-launch path: stage s reads var[s] and writes
-// the other buffer.
-template <typename R>
-__global__ void __launch_bounds__(32 * kApWarps) k_flow(DevTables T, FlowArgs F) {
-  using C = Cx<R>;
-  using V = typename C::T;
-  __shared__ V part[kApWarps][32];
-  cg::cluster_group cluster = cg::this_cluster();
-  const int Cn = (int)cluster.num_blocks(), me = (int)cluster.block_rank();
-  const int wid = threadIdx.x >> 5;
-  const int src_var[5] = {0, 0, 1, 2, 1};
-  for (int sub = 0; sub < F.m; ++sub)
-    for (int st = 1; st <= 4; ++st) {
-      const int var = src_var[st];
-      if (F.first[var].n_tiles > 0) {
-        const ApList& L = F.first[var];
-        for (int tile = me; tile < L.n_tiles; tile += Cn) {
-          ApOut out;
-          int64_t idx, P;
-          const V acc = tile_sum<R>(T, L, tile, 0, 1, part, out, idx, P);
-          if (wid == 0 && idx < P) ((V*)T.bufs[out.dst])[idx] = acc;
-        }
-        cluster.sync();
-      }
-      const ApList& L = F.combine[var];
-      const Epi ep{st, F.y, F.y_lo, st == 2 ? F.ysB : F.ysA, F.acc, F.h};
-      for (int tile = me; tile < L.n_tiles; tile += Cn) {
-        ApOut out;
-        int64_t idx, P;
-        const V acc = tile_sum<R>(T, L, tile, 0, 1, part, out, idx, P);
-        if (wid == 0 && idx < P) tile_store<R>(T, out, ep, idx, acc);
-      }
-      cluster.sync();
-    }
-}
-
 // Launch n_tiles * k CTAs; k > 1 makes every k consecutive CTAs one cluster.
 template <typename Kern, typename... Args>
 static void launch_split(Kern kern, int n_tiles, int k, cudaStream_t s, Args... args) {
@@ -300,33 +260,6 @@ static void launch_split(Kern kern, int n_tiles, int k, cudaStream_t s, Args... 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
-bool launch_flow(int prec, const DevTables& T, const FlowArgs& F, cudaStream_t s) {
-  int tiles = 0;
-  for (int v = 0; v < 3; ++v) tiles = std::max(tiles, std::max(F.first[v].n_tiles, F.combine[v].n_tiles));
-  if (tiles <= 0 || tiles > kFlowMaxTiles) return false;
-  const int C = std::min(tiles, 16);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_flow<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(k_flow<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    attr = true;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)C, 1, 1);
-  cfg.blockDim = dim3(32 * kApWarps, 1, 1);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr1[1];
-  attr1[0].id = cudaLaunchAttributeClusterDimension;
-  attr1[0].val.clusterDim.x = (unsigned)C;
-  attr1[0].val.clusterDim.y = 1;
-  attr1[0].val.clusterDim.z = 1;
-  cfg.attrs = attr1;
-  cfg.numAttrs = 1;
-  if (prec == PREC_F32) return cudaLaunchKernelEx(&cfg, k_flow<float>, T, F) == cudaSuccess;
-  return cudaLaunchKernelEx(&cfg, k_flow<double>, T, F) == cudaSuccess;
 }
 
 void launch_apply(int prec, const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s) {

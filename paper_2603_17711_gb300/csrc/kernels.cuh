@@ -51,24 +51,7 @@ struct DriveArgs {
 };
 
 void launch_apply(int prec, const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s);
-// A whole RK4 flow of a small tensor (every list <= kFlowMaxTiles tiles) in
-// one cluster launch: m substeps x 4 stages of (first list, combine list with
-// the stage epilogue); stage s reads source variant {0,0,1,2,1}[s] and writes
-// ysB at s = 2, ysA otherwise. first[v].n_tiles == 0 means no pair stage.
-// Returns false (nothing launched) when the flow is too large.
-constexpr int kFlowMaxTiles = 64;
-struct FlowArgs {
-  ApList first[3];
-  ApList combine[3];
-  double2* y;
-  void* y_lo;
-  void* ysA;
-  void* ysB;
-  double2* acc;
-  double h;
-  int m;
-};
-bool launch_flow(int prec, const DevTables& T, const FlowArgs& F, cudaStream_t s);
+
 // Mixed form: the same list with its mode products on the tcgen05 tensor
 // cores (tc_apply.cu, 3xTF32). outs_host/terms_host: host copies of the job
 // tables; acc: FP32 scratch of the largest output (RK epilogue lists); flag
