@@ -72,14 +72,17 @@ void launch_qr(double2* U, int d0, int d1, int d2, int leg, double tol, double2*
 // Cluster-parallel variant (qr.cu); returns false when the shape does not fit
 // (bond dim > kQrClusterMaxN or the row blocks exceed shared memory).
 constexpr int kQrClusterMaxN = 64;
+// scratch/scratch_elems: global memory the kernel may use for its Gram / M
+// buffers when shared memory cannot hold them (bond dimensions above ~40).
 bool launch_qr_cluster(double2* U, int d0, int d1, int d2, int leg, double tol, double2* R, int* flag,
-                       float2* U_lo, float2* R_lo, cudaStream_t s);
+                       float2* U_lo, float2* R_lo, double2* scratch, int64_t scratch_elems, cudaStream_t s);
 // Panel of the blocked QR (qr_blocked.cu): the cluster kernel factors columns
 // [c0, c0+nb) of the column-major m x n matrix A over rows [c0, m) with the
 // threshold *thr of the whole matrix (NaN: do nothing), writes V / R entries
 // back in place, beta/alpha/phase/skip of those columns at index c0.., and the
 // panel's WY factor T (nb x nb, row-major) with H_c0..H_{c0+nb-1} = I - V T V^H.
 struct QrPanel {
+  double2* gtail;  // full mode: global scratch (3*C*n*n) for the Gram / M buffers, or null
   double2* A;
   int m, n, c0, nb;
   const double* thr;

@@ -181,9 +181,17 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
   double2* A = smem;
   double2* SU = A + (size_t)n * rp;
   double2* RJ = SU + 32 * (size_t)n;
-  double2* G = RJ + 2 * (size_t)n;
-  double2* GF = G + (size_t)n * n;
-  double2* MM = GF + (size_t)n * n;
+  // Gram / M buffers: shared memory, or (large n) per-CTA regions of pn.gtail
+  const bool gt = !panel && pn.gtail != nullptr;
+  const size_t n2 = (size_t)n * n;
+  double2* G = gt ? pn.gtail + (size_t)me * n2 : RJ + 2 * (size_t)n;
+  double2* GF = gt ? pn.gtail + (size_t)(C + me) * n2 : G + n2;
+  double2* MM = gt ? pn.gtail + (size_t)(2 * C + me) * n2 : GF + n2;
+  // the partial Gram / M of CTA c, as seen from this CTA
+  auto G_of = [&](int c) -> const double2* { return gt ? pn.gtail + (size_t)c * n2 : cluster.map_shared_rank(G, c); };
+  auto MM_of = [&](int c) -> const double2* {
+    return gt ? pn.gtail + (size_t)(2 * C + c) * n2 : cluster.map_shared_rank(MM, c);
+  };
   __shared__ __align__(8) uint64_t mb[2];
   __shared__ double SN[2][16];
   __shared__ double2 SX[2];
@@ -420,7 +428,7 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
     double2 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c)
-      v[c] = c < C ? cluster.map_shared_rank(G, c)[a * n + b] : make_double2(0.0, 0.0);
+      v[c] = c < C ? G_of(c)[a * n + b] : make_double2(0.0, 0.0);
     double2 g = make_double2(0.0, 0.0);
 #pragma unroll
     for (int c = 0; c < 16; ++c)
@@ -481,7 +489,7 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
   }
   cluster.sync();  // every column of M solved; partial Grams no longer read
   // gather M into G (column c from CTA c mod C)
-  for (int t = tid; t < n * n; t += nt) G[t] = cluster.map_shared_rank(MM, (t % n) % C)[t];
+  for (int t = tid; t < n * n; t += nt) G[t] = MM_of((t % n) % C)[t];
   __syncthreads();
   // Q rows: Q[r][c] = delta_rc - sum_{a <= min(r,c)} v_a[r] M[a][c], column c scaled by phase_c
   const int nch = (nr + 31) / 32;
@@ -501,18 +509,32 @@ __global__ void __launch_bounds__(kThreads) k_qr_cluster(double2* U, int d0, int
   cluster.sync();  // keep shared memory alive until every remote read has finished
 }
 
-size_t qr_cluster_smem(int m, int n, int C) {
-  const int rp = (m + C - 1) / C;
-  return sizeof(double2) * ((size_t)n * rp + 34 * (size_t)n + 3 * (size_t)n * n);
-}
+constexpr size_t kQrSmemCap = 200 * 1024;
 
-int qr_cluster_size(int m, int n) {
+size_t qr_cluster_smem(int m, int n, int C, bool gtail) {
+  const int rp = (m + C - 1) / C;
+  return sizeof(double2) * ((size_t)n * rp + 34 * (size_t)n + (gtail ? 0 : 3 * (size_t)n * n));
+}
+size_t qr_cluster_smem(int m, int n, int C) { return qr_cluster_smem(m, n, C, false); }
+
+// Cluster size for an m x n QR (0: does not fit); *gtail set when the Gram / M
+// buffers have to live in global memory.
+int qr_cluster_size(int m, int n, bool* gtail) {
+  *gtail = false;
   if (n > kQrClusterMaxN) return 0;
   int C = (m + 7) / 8;  // about 8 rows per CTA: the factorisation is FP64-issue bound
   C = C < 1 ? 1 : (C > 16 ? 16 : C);
-  while (C > 1 && qr_cluster_smem(m, n, C) > 160 * 1024) --C;  // not expected for C <= 16
-  if (qr_cluster_smem(m, n, C) > 160 * 1024) return 0;
-  return C;
+  if (qr_cluster_smem(m, n, C, false) <= kQrSmemCap) return C;
+  if (qr_cluster_smem(m, n, C, true) <= kQrSmemCap) {
+    *gtail = true;
+    return C;
+  }
+  return 0;
+}
+int qr_cluster_size(int m, int n) {
+  bool gt;
+  const int C = qr_cluster_size(m, n, &gt);
+  return gt ? 0 : C;
 }
 
 template <int G>
@@ -521,13 +543,13 @@ static bool launch_cluster(double2* U, int d0, int d1, int d2, int leg, double t
   static bool attr_done = false;
   if (!attr_done) {
     cudaFuncSetAttribute(k_qr_cluster<G>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(k_qr_cluster<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(k_qr_cluster<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemCap);
     attr_done = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C, 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
-  cfg.dynamicSmemBytes = qr_cluster_smem(m, n, C);
+  cfg.dynamicSmemBytes = qr_cluster_smem(m, n, C, !pn.A && pn.gtail);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -540,20 +562,25 @@ static bool launch_cluster(double2* U, int d0, int d1, int d2, int leg, double t
 }
 
 bool launch_qr_cluster(double2* U, int d0, int d1, int d2, int leg, double tol, double2* R, int* flag,
-                       float2* U_lo, float2* R_lo, cudaStream_t s) {
+                       float2* U_lo, float2* R_lo, double2* scratch, int64_t scratch_elems, cudaStream_t s) {
   const int dd[3] = {d0, d1, d2};
   const int n = dd[leg];
   const int m = (int)((int64_t)d0 * d1 * d2 / n);
-  const int C = qr_cluster_size(m, n);
+  bool gt = false;
+  const int C = qr_cluster_size(m, n, &gt);
   if (C == 0) return false;
   QrPanel pn = {};
+  if (gt) {
+    if (!scratch || scratch_elems < 3 * (int64_t)C * n * n) return false;
+    pn.gtail = scratch;
+  }
   return launch_cluster<8>(U, d0, d1, d2, leg, tol, R, flag, U_lo, R_lo, pn, m, n, C, s);
 }
 
 int qr_panel_cluster(int m_act, int nb) {
   int C = (m_act + 7) / 8;
   C = C < 1 ? 1 : (C > 16 ? 16 : C);
-  return qr_cluster_smem(m_act, nb, C) > 160 * 1024 ? 0 : C;
+  return qr_cluster_smem(m_act, nb, C) > kQrSmemCap ? 0 : C;
 }
 
 bool launch_qr_panel(const QrPanel& pn, cudaStream_t s) {

@@ -279,7 +279,7 @@ bool launch_qr_blocked(double2* U, int d0, int d1, int d2, int leg, double tol, 
   // factorisation: panel, then its reflectors on the trailing columns
   for (int c0 = 0; c0 < n; c0 += kNB) {
     const int nb = std::min(kNB, n - c0);
-    QrPanel pn{A, (int)m, n, c0, nb, sc, beta, alpha, phase, skip, T + (int64_t)(c0 / kNB) * kNB * kNB};
+    QrPanel pn{nullptr, A, (int)m, n, c0, nb, sc, beta, alpha, phase, skip, T + (int64_t)(c0 / kNB) * kNB * kNB};
     if (!launch_qr_panel(pn, s)) return false;
     const int k0 = c0 + nb;
     if (k0 >= n) break;
