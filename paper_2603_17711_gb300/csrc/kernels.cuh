@@ -92,7 +92,7 @@ struct QrPanel {
   int* skip;
   double2* T;
 };
-constexpr int kQrPanelMaxNb = 8;
+constexpr int kQrPanelMaxNb = 16;
 bool launch_qr_panel(const QrPanel& pn, cudaStream_t s);
 int qr_panel_cluster(int m_act, int nb);  // cluster size of a panel, 0 if it does not fit
 // Blocked Householder QR for matrices the cluster kernel cannot hold; same

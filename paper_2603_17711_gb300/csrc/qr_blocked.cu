@@ -152,8 +152,8 @@ __global__ void __launch_bounds__(256) k_qb_zsum(const double2* Ypart, int nblk,
   __shared__ double2 y[kNB];
   if (aborted(sc)) return;
   const int k = k0 + blockIdx.x;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (w < nb) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int w = threadIdx.x >> 5; w < nb; w += nw) {  // warp-uniform
     double2 a = make_double2(0.0, 0.0);
     for (int b = lane; b < nblk; b += 32) {
       const double2 v = Ypart[((int64_t)b * kNB + w) * n + k];
