@@ -279,6 +279,19 @@ ttn_status ttn_rdm_noalloc(const ttn_tree* tree, const int32_t* leg_dims, const 
                            const void* const* node_dev, void* rho_dev, void* stream, char* err,
                            size_t err_len);
 
+/* Autotuner (no counterpart in the paper: GB300 work distribution). Times
+ * every contraction job list of the handle on its stream with each admissible
+ * split (1 .. min(useful, max_split) CTAs per output tile; reps timed launches
+ * each, after one warm-up) and keeps the fastest (a larger split must win by
+ * 3 %). The state is not modified: scratch-writing lists run as they are, RK4
+ * epilogue lists run as stage 1 into scratch, and the environment matrices the
+ * projections overwrite are rebuilt before the next step. Results stay within
+ * rounding of the untuned ones (reduction orders change with the split) and
+ * are deterministic for a given tuning. Changing max_split, or a ps2 rank
+ * change rebuilding a list, returns those lists to the built-in rule.
+ * reps: 1..100. Errors: TTN_ESTATE before ttn_set_workspace, TTN_EINVAL. */
+ttn_status ttn_autotune(ttn_t h, int32_t reps);
+
 const char* ttn_last_error(ttn_t h);
 void ttn_destroy(ttn_t h);
 

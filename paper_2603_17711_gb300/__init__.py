@@ -182,6 +182,9 @@ class TTN:
     def ttn_stats_reset(self) -> None:
         self._check(self.lib.ttn_stats_reset(self.h), "ttn_stats_reset")
 
+    def ttn_autotune(self, reps: int = 3) -> None:
+        self._check(self.lib.ttn_autotune(self.h, int(reps)), "ttn_autotune")
+
     def ttn_split_log(self):
         """(features [n, 24] float32, classes [n] int32) of the full-SVD ps2 splits so far."""
         n = C.c_int32()

@@ -64,6 +64,7 @@ SIGNATURES = [
     ("ttn_profile", C.c_int, [_h, C.c_int32]),
     ("ttn_profile_read", C.c_int, [_h, C.c_int32, _f64p]),
     ("ttn_stats_reset", C.c_int, [_h]),
+    ("ttn_autotune", C.c_int, [_h, C.c_int32]),
     ("ttn_rdm_noalloc", C.c_int, [C.POINTER(ttn_tree), _i32p, _i32p, C.POINTER(C.c_void_p), C.c_void_p,
                                   C.c_void_p, C.c_char_p, C.c_size_t]),
     ("ttn_mlp_n_params", C.c_int, [_i32p]),

@@ -1284,6 +1284,94 @@ ttn_status ttn_profile_read(ttn_t h, int32_t kind, double* ms) {
   return TTN_OK;
 }
 
+ttn_status ttn_autotune(ttn_t h, int32_t reps) {
+  return guarded(h, [&]() -> ttn_status {
+    if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
+    if (reps < 1 || reps > 100) return h->fail(TTN_EINVAL, "reps must be 1..100");
+    Plan& p = h->plan;
+    cudaStream_t s = h->stream;
+    std::vector<char> f64(p.ap_lists.size(), 0);  // absorb lists run in FP64 in both forms
+    for (const auto& a : p.absorb)
+      for (int id : a)
+        if (id >= 0) f64[id] = 1;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(h, cudaEventCreate(&e0));
+    CUDA_TRY(h, cudaEventCreate(&e1));
+    auto time_of = [&](auto&& launch) -> float {
+      launch();  // warm
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps; ++r) launch();
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      return ms;
+    };
+    // lists writing scratch outputs run as they are; lists with an RK
+    // epilogue run as stage 1 into scratch (tmp read, acc / ys2 written), so
+    // the state is untouched; the environment matrices the projections
+    // overwrite are rebuilt before the next step
+    const Epi store{EPI_STORE, nullptr, nullptr, nullptr, nullptr, 0.0};
+    const Epi rk1{EPI_RK1, h->h_bufs[p.buf.tmp], h->h_bufs_lo[p.buf.tmp], h->h_bufs_lo[p.buf.ys2],
+                  h->h_bufs[p.buf.acc], 0.0};
+    const int cap = std::min(kMaxSplit, h->params.max_split);
+    for (size_t i = 0; i < p.ap_lists.size(); ++i) {
+      ApList& L = p.ap_lists[i];
+      if (L.n_tiles <= 0) continue;
+      const int prec = f64[i] ? PREC_F64 : h->prec;
+      const DevTables& T = f64[i] ? h->T : h->Tlo;
+      if (!f64[i] && h->prec == PREC_F32 && h->params.tensor_cores &&
+          tc_applicable(L, p.ap_outs.data(), p.ap_terms.data()))
+        continue;
+      const bool epi = p.ap_outs[L.out_begin].dst < 0;
+      int best = 1;
+      float tb = 3.4e38f;
+      // splits only pay below a few CTAs per SM: larger lists keep one CTA per tile
+      const int kmax = std::max(1, std::min(std::min(L.useful, cap), 4 * p.sm_count / L.n_tiles));
+      if (kmax == 1) {
+        L.k = 1;
+        continue;
+      }
+      for (int k = 1; k <= kmax; ++k) {
+        ApList L2 = L;
+        L2.k = k;
+        const float t = time_of([&] { launch_apply(prec, T, L2, epi ? rk1 : store, s); });
+        if (t < 0.97f * tb) {  // a larger split must win by 3 %
+          tb = t;
+          best = k;
+        }
+      }
+      L.k = best;
+    }
+    for (PjList& L : p.pj_lists) {
+      if (L.n_tiles <= 0) continue;
+      int best = L.k;
+      float tb = 3.4e38f;
+      const int kmax = std::max(1, std::min(std::min(L.useful, cap), 4 * p.sm_count / L.n_tiles));
+      if (kmax == 1) {
+        L.k = 1;
+        continue;
+      }
+      for (int k = 1; k <= kmax; ++k) {
+        PjList L2 = L;
+        L2.k = k;
+        const float t = time_of([&] { launch_project(h->prec, h->Tlo, L2, s); });
+        if (t < 0.97f * tb) {
+          tb = t;
+          best = k;
+        }
+      }
+      L.k = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CUDA_TRY(h, cudaGetLastError());
+    h->envs_dirty = true;
+    h->drop_graph();
+    return TTN_OK;
+  });
+}
+
 ttn_status ttn_stats_reset(ttn_t h) {
   if (!h) return TTN_EINVAL;
   CUDA_TRY(h, h->drain_marks());

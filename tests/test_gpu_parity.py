@@ -364,3 +364,23 @@ def test_ps2_and_ps1_runs_are_bitwise_repeatable(pkg):
             runs.append(np.array(traj))
             g.close()
         assert np.array_equal(runs[0], runs[1]) and np.array_equal(runs[0], runs[2]), scheme
+
+
+def test_autotuned_handle_matches_oracle(pkg):
+    """ttn_autotune changes only launch shapes: the trajectory stays on the
+    oracle's, in FP64 and in the mixed form, and tuning twice is harmless."""
+    w = W.exciton_chain(n_sites=3, rank=7, depth=4, n_steps=6)
+    for prec, tol in ((pkg.TTN_FP64, TOL_SHORT), (pkg.TTN_MIXED_FP32, 1e-6)):
+        g = gpu_from(pkg, w, precision=prec)
+        o = ottn.from_workload(w)
+        g.ttn_step(w.dt, pkg.TTN_PS1, 1)
+        o.step(w.dt, "ps1")
+        g.ttn_autotune(2)
+        g.ttn_autotune(1)
+        err = float(np.max(np.abs(g.ttn_rdm() - o.rdm())))
+        for _ in range(5):
+            g.ttn_step(w.dt, pkg.TTN_PS1, 1)
+            o.step(w.dt, "ps1")
+            err = max(err, float(np.max(np.abs(g.ttn_rdm() - o.rdm()))))
+        g.close()
+        assert err <= tol, (prec, err)
