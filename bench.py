@@ -34,6 +34,7 @@ METRIC = "HEOM-TTN steps/s & node-contraction TFLOP/s vs plain FP64 at RDM err <
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2 FP64 FMA/clk/SM x ~2.07 GHz)
 WORKLOAD = "7-site Frenkel exciton chain, 21 features (1 Drude + 2 Pade per site), depth 8, BTT, rank 20, ps1, dt 0.05 fs"
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+APPLY_DRAM_BYTES = 139524   # ncu: mean DRAM bytes (read + write) per k_apply launch of one timed step
 
 
 def workload():
@@ -348,7 +349,10 @@ def bench_ours(args, rank, world, local_rank):
                    if tune_s is not None else "built-in rule"},
         "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "traffic": None, "peak_source": "nominal FP64 (recipe table; not in MEASURED_PEAKS.json)",
+                     "traffic": APPLY_DRAM_BYTES if names[dom].startswith("node/bond") else None,
+                     "traffic_source": "mean dram__bytes_read+write per k_apply launch, ncu capture of 60 launches "
+                                       "(profiles/apply_traffic_exciton7_r20_fp64.md)",
+                     "peak_source": "nominal FP64 (recipe table; not in MEASURED_PEAKS.json)",
                      "launches_per_step": n_l / args.steps},
         "node_contraction": {"tflops_kernel": (k1_flops / (k1_ms * 1e-3) / 1e12) if k1_ms > 0 else None,
                              "tflops_step": flops[0] / (ms_max * 1e-3) / 1e12,
