@@ -92,35 +92,59 @@ __device__ __forceinline__ Geo3 geo_of(const ApOut& o) {
 // M[i][x] and B[n][2x+c'] = component c' of X at (x, position n). A chunk of
 // 32 K columns covers 16 leg indices x; each complex value is read once.
 // base[nn]: offset of tile position nn over the two other legs.
-__device__ void stage_chunk(float* buf, const float2* __restrict__ M, const float2* __restrict__ X, int d,
-                            int64_t st_l, bool x_fast, const int64_t* base, int nvalid, int kc) {
+constexpr int kAq = (kTcM / 2) * (kTcK / 2) / kTcThreads;  // complex operator entries per thread and chunk
+constexpr int kBq = kTcN * (kTcK / 2) / kTcThreads;        // complex tensor entries per thread and chunk
+struct ChunkRegs {
+  float2 m[kAq], x[kBq];
+};
+
+// Load this thread's share of chunk kc (one L2 round trip; the values are
+// split and stored later, so the loads overlap the MMAs of the previous chunk).
+__device__ __forceinline__ void load_chunk(ChunkRegs& r, const float2* __restrict__ M, const float2* __restrict__ X,
+                                           int d, int64_t st_l, bool x_fast, const int64_t* base, int nvalid,
+                                           int kc) {
+  const int x0 = kc * (kTcK / 2);
+#pragma unroll
+  for (int q = 0; q < kAq; ++q) {
+    const int e = threadIdx.x + q * kTcThreads, i = e >> 4, x = x0 + (e & 15);
+    r.m[q] = (i < d && x < d) ? M[i * d + x] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int q = 0; q < kBq; ++q) {
+    // consecutive threads walk the contiguous direction of X
+    const int e = threadIdx.x + q * kTcThreads;
+    const int nn = x_fast ? e >> 4 : e % kTcN, x = x0 + (x_fast ? e & 15 : e / kTcN);
+    r.x[q] = (nn < nvalid && x < d) ? X[(int64_t)x * st_l + base[nn]] : make_float2(0.f, 0.f);
+  }
+}
+// Split into tf32 hi / lo, embed, and store into one stage buffer.
+__device__ __forceinline__ void store_chunk(float* buf, const ChunkRegs& r, bool x_fast) {
   float* Ah = buf;
   float* Al = buf + kAElems;
   float* Bh = buf + 2 * kAElems;
   float* Bl = Bh + kBElems;
-  const int x0 = kc * (kTcK / 2);
-  for (int e = threadIdx.x; e < (kTcM / 2) * (kTcK / 2); e += kTcThreads) {
-    const int i = e >> 4, xl = e & 15, x = x0 + xl;
-    const float2 m = (i < d && x < d) ? M[i * d + x] : make_float2(0.f, 0.f);
-    const float v[4] = {m.x, -m.y, m.y, m.x};  // (c, c') = (0,0), (0,1), (1,0), (1,1)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int o = cm_off(2 * i + (q >> 1), 2 * xl + (q & 1));
-      const float h = tf32_hi(v[q]);
+  for (int q = 0; q < kAq; ++q) {
+    const int e = threadIdx.x + q * kTcThreads, i = e >> 4, xl = e & 15;
+    const float v[4] = {r.m[q].x, -r.m[q].y, r.m[q].y, r.m[q].x};  // (c, c') = (0,0), (0,1), (1,0), (1,1)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int o = cm_off(2 * i + (t >> 1), 2 * xl + (t & 1));
+      const float h = tf32_hi(v[t]);
       Ah[o] = h;
-      Al[o] = tf32_hi(v[q] - h);
+      Al[o] = tf32_hi(v[t] - h);
     }
   }
-  for (int e = threadIdx.x; e < kTcN * (kTcK / 2); e += kTcThreads) {
-    // consecutive threads walk the contiguous direction of X
-    const int nn = x_fast ? e >> 4 : e % kTcN, xl = x_fast ? e & 15 : e / kTcN, x = x0 + xl;
-    const float2 v = (nn < nvalid && x < d) ? X[(int64_t)x * st_l + base[nn]] : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < kBq; ++q) {
+    const int e = threadIdx.x + q * kTcThreads;
+    const int nn = x_fast ? e >> 4 : e % kTcN, xl = x_fast ? e & 15 : e / kTcN;
     const int o0 = cm_off(nn, 2 * xl), o1 = cm_off(nn, 2 * xl + 1);
-    const float h0 = tf32_hi(v.x), h1 = tf32_hi(v.y);
+    const float h0 = tf32_hi(r.x[q].x), h1 = tf32_hi(r.x[q].y);
     Bh[o0] = h0;
-    Bl[o0] = tf32_hi(v.x - h0);
+    Bl[o0] = tf32_hi(r.x[q].x - h0);
     Bh[o1] = h1;
-    Bl[o1] = tf32_hi(v.y - h1);
+    Bl[o1] = tf32_hi(r.x[q].y - h1);
   }
 }
 
@@ -202,11 +226,13 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
       }
     }
   };
+  ChunkRegs regs;
   {
     const float2 *M, *X;
     int kc;
     chunk_src(0, M, X, kc);
-    stage_chunk(tsm, M, X, d, g.st[leg], leg == 2, base, nvalid, kc);
+    load_chunk(regs, M, X, d, g.st[leg], leg == 2, base, nvalid, kc);
+    store_chunk(tsm, regs, leg == 2);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -238,15 +264,16 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
                    : "memory");
     }
     if (ci + 1 < nchunks) {
+      const float2 *M, *X;
+      int kc;
+      chunk_src(ci + 1, M, X, kc);
+      load_chunk(regs, M, X, d, g.st[leg], leg == 2, base, nvalid, kc);
       // the other stage is free once the MMAs of chunk ci-1 have completed
       if (ci >= 1 && ok) {
         ok = mbar_wait(&mbar[b ^ 1], ph[b ^ 1], deadline);
         ph[b ^ 1] ^= 1u;
       }
-      const float2 *M, *X;
-      int kc;
-      chunk_src(ci + 1, M, X, kc);
-      stage_chunk(tsm + (b ^ 1) * kStageFloats, M, X, d, g.st[leg], leg == 2, base, nvalid, kc);
+      store_chunk(tsm + (b ^ 1) * kStageFloats, regs, leg == 2);
     }
   }
   // all MMAs done once the last commit has landed (they complete in order)
