@@ -54,7 +54,7 @@ typedef enum {
   TTN_ENUMERIC = 4,      /* non-finite value detected in the state */
   TTN_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
   TTN_ESTATE = 6,        /* call out of order (e.g. ttn_step before sop_load) */
-  TTN_EUNSUPPORTED = 7   /* valid request this build does not implement */
+  TTN_EUNSUPPORTED = 7   /* valid request the library does not implement */
 } ttn_status;
 
 /* Arithmetic of the node and bond contractions. QR, SVD, RK4 stage
