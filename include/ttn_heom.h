@@ -82,9 +82,9 @@ typedef struct {
  *                    m = max(1, ceil(|tau| * Lambda / kappa - 1e-9)), Lambda =
  *                    sum over terms of |coef| * prod ||op||_2 (|coef| * g_bound
  *                    for driven terms), fixed at sop_load.
- *  ps2_atol  (1e-7)  ps2 keeps r0 = #{sigma > ps2_atol} ... (Sec. 5.3, Table 4)
+ *  ps2_atol  (1e-7)  ps2 keeps r0 = #{sigma > ps2_atol} ... (Sec. 4, Table 4)
  *  ps2_ratio (2)     ... and then min(cap, max(1, ceil(ps2_ratio * r0))) values.
- *  max_rank  (32)    ps2 bond-rank cap (Sec. 5.3, max_auxiliary_rank).
+ *  max_rank  (32)    ps2 bond-rank cap (Sec. 4, Table 4: max_auxiliary_rank).
  *  svd_tol   (1e-12) kept singular values <= svd_tol*sigma_1 are replaced by a
  *                    deterministic completion with zero weight.
  *  max_split (8)     1..8: at most this many CTAs (one thread-block cluster)
@@ -188,7 +188,7 @@ ttn_status ttn_node_shape(ttn_t h, int32_t u, int32_t* dims3);
  * semiunitary); environments are rebuilt before the next step. Synchronises. */
 ttn_status ttn_get_node(ttn_t h, int32_t u, double* host_out);
 ttn_status ttn_set_node(ttn_t h, int32_t u, const double* host_in);
-/* Simulation time reached (starts at 0, Sec. 5.1 checkpoint convention). */
+/* Simulation time reached (starts at 0, Sec. 7.1 checkpoint convention). */
 ttn_status ttn_time(ttn_t h, double* t);
 /* RK4 substeps used for a flow of length tau under the current generator. */
 ttn_status ttn_substeps(ttn_t h, double tau, int32_t* m);

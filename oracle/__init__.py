@@ -11,7 +11,7 @@ Modules
             Eq. DL, Eq. BO; Pade decomposition of the Bose function).
   sop    -- the 5K+2 sum-of-products terms of the bexcitonic HEOM generator
             (Eq. heom-std, Eq. dissipator, Eq. master_lvn) with a metric choice
-            (Sec. 5.2 / Listing custommetric).
+            (Sec. 7.4, Listing custommetric).
   dense  -- brute-force dense hierarchy: dOmega/dt = L Omega on the full
             M*M*prod(N_k) vector (Eq. EDO-eom).
   ttn    -- tree tensor network state, environments, effective operators,

@@ -23,7 +23,7 @@ product terms (Eq. master_lvn):
 A time-dependent system term g_d(t) V_d adds -i g_d V_d on leg i and
 +i g_d conj(V_d) on leg j.
 
-The metric z_k is diagonal in n (Sec. 5.2): ``'abs'`` uses the constant
+The metric z_k is diagonal in n (Sec. 7.4): ``'abs'`` uses the constant
 z = f_k with f_k = sqrt((|c_k| + |cbar_k|)/2) (Listing custommetric; f_k = 1
 when c_k = cbar_k = 0, where the abs rule would give a singular metric);
 ``'conventional'`` uses z(n) = i n^{-1/2} (z(0) = i), the conventional HEOM
@@ -60,7 +60,7 @@ def ladder(N: int):
 
 
 def metric_diag(N: int, c: complex, cb: complex, metric) -> np.ndarray:
-    """Diagonal of z_k in the number basis (Sec. 5.2)."""
+    """Diagonal of z_k in the number basis (Sec. 7.4)."""
     if metric == "abs":
         f = np.sqrt((abs(c) + abs(cb)) / 2.0)
         # a feature with c = cbar = 0 never feeds the hierarchy; any invertible

@@ -28,7 +28,7 @@ Plain numpy complex128 restatement of the TTN-HEOM hot path (Sec. 2.3):
   adjacent root flows are merged into one flow of dt. A time-dependent system
   term is frozen at t0 + dt/4 during the first half and t0 + 3dt/4 during the
   second.
-* ps2 (adaptive rank, Sec. 2.3 last paragraph and Sec. 5.3): neighbouring cores
+* ps2 (adaptive rank, Sec. 2.3 last paragraph and Sec. 7.5): neighbouring cores
   are merged, the pair is propagated, and an SVD splits it back with a
   truncated rank.
 * Sub-flows use classical RK4 with m = max(1, ceil(|tau| Lambda / 2.5)) substeps,
@@ -473,7 +473,7 @@ class TTN:
 
     def truncation_rank(self, s: np.ndarray, cap: int) -> int:
         """r0 = #{sigma > ps2_atol}; keep min(cap, max(1, ceil(ps2_ratio * r0)))
-        (reading of Sec. 5.3: a ps2_ratio multiple of the kept count re-admits a
+        (reading of Sec. 7.5: a ps2_ratio multiple of the kept count re-admits a
         part of the discarded singular values)."""
         p = self.params
         r0 = int(np.sum(s > p.ps2_atol))

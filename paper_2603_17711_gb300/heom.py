@@ -8,7 +8,7 @@ Turns physical parameters into the arrays that ``sop_load`` takes:
   (Eq. BO) spectral densities, with Pade (Hu-Xu-Yan) or Matsubara Bose poles;
 * the 5K+2 product terms of the bexcitonic HEOM generator (Eq. heom-std,
   Eq. dissipator, Eq. master_lvn) with the 'abs' metric z_k = f_k,
-  f_k = sqrt((|c_k| + |cbar_k|)/2) (Sec. 5.2), packed for the C ABI.
+  f_k = sqrt((|c_k| + |cbar_k|)/2) (Sec. 7.4), packed for the C ABI.
 
 Each distinct local operator is registered once per leg (Q_b and conj(Q_b) on
 the system legs once per bath), which lets the library group the two-leg

@@ -1,7 +1,7 @@
 """Pins for oracle.sop (Eq. heom-std, Eq. dissipator, Eq. master_lvn): the dense
 generator assembled from the product terms equals an independently written
 textbook HEOM in ADM-index form (conventional metric, Sec. 2.2), the term count
-is 5K+2, and the reduced density matrix does not depend on the metric (Sec. 5.2)."""
+is 5K+2, and the reduced density matrix does not depend on the metric (Sec. 7.4)."""
 import itertools
 
 import numpy as np
