@@ -53,6 +53,13 @@ struct ttn_ctx {
   double2* qr_work = nullptr;
   int64_t qr_elems = 0;
   float2* tc_acc = nullptr;  // FP32 scratch of the tensor-core path (mixed form)
+  // pre-split operator matrices of the tensor-core path: on when some job list
+  // was tensor-core eligible at bind time; every writer of those matrices
+  // then refreshes their pool copies
+  bool tc_pool_on = false;
+  float* tc_pool = nullptr;
+  int64_t* tc_off_dev = nullptr;
+  std::vector<int64_t> tc_off;
   // ps2 scratch
   double2 *svd_A = nullptr, *svd_V = nullptr, *svd_Z = nullptr, *svd_Zg = nullptr, *svd_C = nullptr;
   double* svd_sigma = nullptr;
@@ -175,6 +182,8 @@ ttn_status cuda_fail(ttn_t h, cudaError_t e, const char* what) {
 struct Layout {
   size_t nodes, pool, scratch, qr, rdm, rho, bufs_tab, mats_tab, terms, outs, pjs, drives, flag, total;
   size_t nodes32 = 0, pool32 = 0, scratch32 = 0, bufs_tab_lo = 0, mats_tab_lo = 0, tc_acc = 0;  // FP32 mode only
+  size_t tc_pool = 0, tc_off = 0;
+  std::vector<int64_t> tc_off_host;  // float offset of each matrix in tc_pool, -1 if none
   size_t svd_small = 0, rsvd = 0, mlp = 0;
   std::vector<int64_t> node_off;  // complex elements from `nodes`
   std::vector<int64_t> rdm_off;
@@ -239,6 +248,21 @@ Layout layout_of(const Plan& p, int prec) {
     L.scratch32 = take(((int64_t)(2 + p.buf.n_t + p.buf.n_w) * S + 3 * r2 + 3 * p.theta_cap) * sizeof(float2));
     L.bufs_tab_lo = take(p.buf.n_bufs * sizeof(void*));
     L.tc_acc = take(S * sizeof(float2));
+    // pre-split copies of the operator matrices the job lists use (not the bond matrix)
+    L.tc_off_host.assign(p.mats.size(), -1);
+    std::vector<char> used(p.mats.size(), 0);
+    for (const ApTerm& t : p.ap_terms)
+      if (t.mat >= 0) used[t.mat] = 1;
+    int64_t pf = 0;
+    for (size_t i = 0; i < p.mats.size(); ++i) {
+      if (!used[i] || (int)i == p.bond_mat) continue;
+      const int64_t f = tc_pool_floats(p.mats[i].d);
+      if (f == 0) continue;
+      L.tc_off_host[i] = pf;
+      pf += f;
+    }
+    L.tc_pool = take(std::max<int64_t>(pf, 1) * sizeof(float));
+    L.tc_off = take(p.mats.size() * sizeof(int64_t));
     L.mats_tab_lo = take(p.mats.size() * sizeof(void*));
   }
   L.total = off;
@@ -277,7 +301,8 @@ struct Exec {
     if (h->prec == PREC_F32 && h->params.tensor_cores && h->tc_acc &&
         tc_applicable(L, p.ap_outs.data(), p.ap_terms.data())) {
       run(kind, L.flops, [&] {
-        if (!launch_apply_tc(h->Tlo, L, e, p.ap_outs.data(), p.ap_terms.data(), h->tc_acc, h->flag_dev, s))
+        if (!launch_apply_tc(h->Tlo, L, e, p.ap_outs.data(), p.ap_terms.data(), h->tc_acc, h->flag_dev,
+                             h->tc_pool_on ? h->tc_pool : nullptr, h->tc_pool_on ? h->tc_off_dev : nullptr, s))
           launch_apply(h->prec, h->Tlo, L, e, s);
       });
       return;
@@ -293,6 +318,13 @@ struct Exec {
     if (E.project >= 0) {
       const PjList& L = p.pj_lists[E.project];
       run(1, L.flops, [&] { launch_project(h->prec, h->Tlo, L, s); });
+      if (h->tc_pool_on) {
+        const int d = p.dims[a][p.tree.leg_index(a, b)];  // current rank of the bond
+        std::vector<TcEmbedJob> jobs;
+        for (int slot : p.dir_slots[p.dir_id(a, b)])
+          if (slot >= 0 && h->tc_off[slot] >= 0) jobs.push_back(TcEmbedJob{slot, d, h->tc_off[slot]});
+        run(1, 0.0, [&] { launch_tc_embed(h->Tlo.mats, jobs.data(), (int)jobs.size(), h->tc_pool, s); });
+      }
     }
   }
   // U_u := Q (semi-unitary toward neighbour v), R -> bond buffer
@@ -376,6 +408,12 @@ struct Exec {
     run(3, 0.0, [&] {
       launch_drive((double2* const*)h->T.mats, m32, h->drive_list_dev, (int)h->drive_list.size(), g, s);
     });
+    if (h->tc_pool_on) {
+      std::vector<TcEmbedJob> jobs;
+      for (const DriveMat& dm : h->drive_list)
+        if (h->tc_off[dm.cur] >= 0) jobs.push_back(TcEmbedJob{dm.cur, dm.d, h->tc_off[dm.cur]});
+      run(3, 0.0, [&] { launch_tc_embed(h->Tlo.mats, jobs.data(), (int)jobs.size(), h->tc_pool, s); });
+    }
   }
   void step_ps1(double dt, double t0) {
     const double hh = 0.5 * dt;
@@ -960,6 +998,12 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
         h->h_mats_lo[i] = p.mats[i].off >= 0 ? (void*)(p32 + p.mats[i].off) : nullptr;
       h->h_mats_lo[p.bond_mat] = h->h_bufs_lo[p.buf.bond_y];
       h->tc_acc = (float2*)(base + L.tc_acc);
+      h->tc_pool = (float*)(base + L.tc_pool);
+      h->tc_off_dev = (int64_t*)(base + L.tc_off);
+      h->tc_off = L.tc_off_host;
+      h->tc_pool_on = false;
+      for (const ApList& al : p.ap_lists)
+        h->tc_pool_on = h->tc_pool_on || (al.n_tiles > 0 && tc_applicable(al, p.ap_outs.data(), p.ap_terms.data()));
       h->Tlo.bufs = (void* const*)(base + L.bufs_tab_lo);
       h->Tlo.mats = (void* const*)(base + L.mats_tab_lo);
     }
@@ -972,6 +1016,8 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
       CUDA_TRY(h, cudaMemcpyAsync((void*)h->Tlo.bufs, h->h_bufs_lo.data(), h->h_bufs_lo.size() * sizeof(void*),
                                   cudaMemcpyHostToDevice, s));
       CUDA_TRY(h, cudaMemcpyAsync((void*)h->Tlo.mats, h->h_mats_lo.data(), h->h_mats_lo.size() * sizeof(void*),
+                                  cudaMemcpyHostToDevice, s));
+      CUDA_TRY(h, cudaMemcpyAsync(h->tc_off_dev, h->tc_off.data(), h->tc_off.size() * sizeof(int64_t),
                                   cudaMemcpyHostToDevice, s));
       CUDA_TRY(h, cudaStreamSynchronize(s));
     }
@@ -1023,6 +1069,13 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
       CUDA_TRY(h, cudaMemcpyAsync(h->drive_list_dev, h->drive_list.data(), h->drive_list.size() * sizeof(DriveMat),
                                   cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s));
+    if (h->tc_pool_on) {  // pool copies of the open-leg operators (classes follow with every env update)
+      std::vector<TcEmbedJob> jobs;
+      for (const LocalMat& lm : p.locals)
+        if (h->tc_off[lm.slot] >= 0) jobs.push_back(TcEmbedJob{lm.slot, p.leg_dims[lm.leg], h->tc_off[lm.slot]});
+      launch_tc_embed(h->Tlo.mats, jobs.data(), (int)jobs.size(), h->tc_pool, s);
+      CUDA_TRY(h, cudaGetLastError());
+    }
     CUDA_TRY(h, cudaStreamSynchronize(s));
     h->ws_bound = true;
     h->init_ranks = p.ranks;

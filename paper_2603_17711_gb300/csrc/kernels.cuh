@@ -57,9 +57,27 @@ void launch_apply(int prec, const DevTables& T, const ApList& L, const Epi& e, c
 // tables; acc: FP32 scratch of the largest output (RK epilogue lists); flag
 // bit 3 on a timed-out MMA wait. tc_applicable: 3-leg outputs, contracted
 // legs of dimension <= 64, largest output >= 16384 elements.
+// pool/pool_off (nullable): pre-split operator matrices (launch_tc_embed),
+// pool_off[mat] the float offset of a matrix or -1 (staged by the threads).
 bool tc_applicable(const ApList& L, const ApOut* outs_host, const ApTerm* terms_host);
 bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const ApOut* outs_host,
-                     const ApTerm* terms_host, float2* acc, int* flag, cudaStream_t s);
+                     const ApTerm* terms_host, float2* acc, int* flag, const float* pool, const int64_t* pool_off,
+                     cudaStream_t s);
+// Pre-split copies of FP32 operator matrices for the tensor-core path: for
+// each job, matrix `mat` (d x d, d <= 64) of the FP32 matrix table is embedded
+// and split into tf32 hi / lo in the layout the apply kernel stages, at float
+// offset `off` of pool (tc_pool_floats(d) floats, 0 when d > 64).
+struct TcEmbedJob {
+  int mat, d;
+  int64_t off;
+};
+constexpr int kTcEmbedBatch = 32;
+struct TcEmbedBatch {
+  int n;
+  TcEmbedJob job[kTcEmbedBatch];
+};
+int64_t tc_pool_floats(int d);
+void launch_tc_embed(void* const* mats32, const TcEmbedJob* jobs, int n, float* pool, cudaStream_t s);
 void launch_project(int prec, const DevTables& T, const PjList& L, cudaStream_t s);
 // Householder QR of node tensor U (dims d[3]) matricised toward leg `leg`.
 // U is overwritten with Q (same layout), R (d_leg x d_leg, row-major) written to R.

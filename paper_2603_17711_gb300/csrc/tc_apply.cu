@@ -13,8 +13,11 @@
 // products hi*hi + hi*lo + lo*hi are accumulated in FP32 ("3xTF32"), which
 // keeps the error at the level of FP32 CUDA-core arithmetic.
 //
-// Operands are staged by the threads (the 2x2 embedding and the hi/lo split
-// happen on the way) into shared memory in the K-major, unswizzled canonical
+// The operator operand comes pre-split from a pool that every writer of an
+// operator matrix refreshes (launch_tc_embed) and is copied into shared memory
+// with one bulk asynchronous copy per chunk; the tensor operand is staged by
+// the threads (the 2x2 embedding and the hi/lo split happen on the way) into
+// shared memory in the K-major, unswizzled canonical
 // layout: 8-row x 16-byte core matrices, K-adjacent core matrices 128 B apart
 // (leading byte offset), 8-row groups 1024 B apart (stride byte offset). Two
 // stages alternate so that staging chunk c+1 overlaps the MMAs of chunk c;
@@ -102,10 +105,10 @@ struct ChunkRegs {
 // split and stored later, so the loads overlap the MMAs of the previous chunk).
 __device__ __forceinline__ void load_chunk(ChunkRegs& r, const float2* __restrict__ M, const float2* __restrict__ X,
                                            int d, int64_t st_l, bool x_fast, const int64_t* base, int nvalid,
-                                           int kc) {
+                                           int kc, bool with_a) {
   const int x0 = kc * (kTcK / 2);
 #pragma unroll
-  for (int q = 0; q < kAq; ++q) {
+  for (int q = 0; q < kAq && with_a; ++q) {
     const int e = threadIdx.x + q * kTcThreads, i = e >> 4, x = x0 + (e & 15);
     r.m[q] = (i < d && x < d) ? M[i * d + x] : make_float2(0.f, 0.f);
   }
@@ -118,13 +121,14 @@ __device__ __forceinline__ void load_chunk(ChunkRegs& r, const float2* __restric
   }
 }
 // Split into tf32 hi / lo, embed, and store into one stage buffer.
-__device__ __forceinline__ void store_chunk(float* buf, const ChunkRegs& r, bool x_fast) {
+__device__ __forceinline__ void store_chunk(float* buf, const ChunkRegs& r, bool x_fast, bool with_a,
+                                            bool with_b = true) {
   float* Ah = buf;
   float* Al = buf + kAElems;
   float* Bh = buf + 2 * kAElems;
   float* Bl = Bh + kBElems;
 #pragma unroll
-  for (int q = 0; q < kAq; ++q) {
+  for (int q = 0; q < kAq && with_a; ++q) {
     const int e = threadIdx.x + q * kTcThreads, i = e >> 4, xl = e & 15;
     const float v[4] = {r.m[q].x, -r.m[q].y, r.m[q].y, r.m[q].x};  // (c, c') = (0,0), (0,1), (1,0), (1,1)
 #pragma unroll
@@ -136,7 +140,7 @@ __device__ __forceinline__ void store_chunk(float* buf, const ChunkRegs& r, bool
     }
   }
 #pragma unroll
-  for (int q = 0; q < kBq; ++q) {
+  for (int q = 0; q < kBq && with_b; ++q) {
     const int e = threadIdx.x + q * kTcThreads;
     const int nn = x_fast ? e >> 4 : e % kTcN, xl = x_fast ? e & 15 : e / kTcN;
     const int o0 = cm_off(nn, 2 * xl), o1 = cm_off(nn, 2 * xl + 1);
@@ -148,13 +152,34 @@ __device__ __forceinline__ void store_chunk(float* buf, const ChunkRegs& r, bool
   }
 }
 
+// Pre-split operator matrices: the A operand of every K chunk of a matrix,
+// embedded and split exactly as the staging above would (hi then lo, each
+// kTcM x kTcK floats in the canonical layout), so the apply kernel can copy a
+// chunk with one bulk asynchronous copy. One CTA per (job, chunk).
+__global__ void k_tc_embed(void* const* mats32, TcEmbedBatch jb, float* pool) {
+  const TcEmbedJob j = jb.job[blockIdx.x];
+  const int kc = blockIdx.y;
+  if (kc >= (2 * j.d + kTcK - 1) / kTcK) return;
+  const float2* M = (const float2*)mats32[j.mat];
+  float* out = pool + j.off + (int64_t)kc * 2 * kAElems;
+  ChunkRegs r;
+  const int x0 = kc * (kTcK / 2);
+#pragma unroll
+  for (int q = 0; q < kAq; ++q) {
+    const int e = threadIdx.x + q * kTcThreads, i = e >> 4, x = x0 + (e & 15);
+    r.m[q] = (i < j.d && x < j.d) ? M[i * j.d + x] : make_float2(0.f, 0.f);
+  }
+  store_chunk(out, r, false, true, false);  // the A hi / lo halves only
+}
+
 // One CTA = one (output, 64-position tile) of leg `leg`: Y_o (+)= sum over the
 // output's terms on this leg of M_t x_leg X_t. Y_o is the STORE destination
 // (or acc for an RK epilogue list); the first leg with terms writes, later
 // legs add. Flag bit 3 on a timed-out MMA wait.
-__global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, int leg, float2* acc, int* flag) {
+__global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, int leg, float2* acc, int* flag,
+                                                        const float* pool, const int64_t* pool_off) {
   extern __shared__ __align__(128) float tsm[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t mbar[2], lbar[2];  // MMA commits, bulk A copies
   __shared__ uint32_t tmem_base;
   __shared__ int64_t base[kTcN];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -199,6 +224,8 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&lbar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&lbar[1])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -210,10 +237,11 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
   const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
   const uint64_t deadline = gtimer() + 1000000000ull;
   bool ok = true;
-  uint32_t ph[2] = {0u, 0u};
+  uint32_t ph[2] = {0u, 0u}, lph[2] = {0u, 0u};
 
   // chunk ci -> (term, kc)
-  auto chunk_src = [&](int ci, const float2*& M, const float2*& X, int& kc) {
+  // chunk ci -> (operator, tensor, K chunk); poff: pre-split operator offset or -1
+  auto chunk_src = [&](int ci, const float2*& M, const float2*& X, int& kc, int64_t& poff) {
     int k = ci / nkc;
     kc = ci % nkc;
     for (int t = out.term_begin; t < out.term_end; ++t) {
@@ -222,17 +250,35 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
       if (k-- == 0) {
         M = (const float2*)T.mats[tm.mat];
         X = (const float2*)T.bufs[tm.src];
+        poff = pool_off ? pool_off[tm.mat] : -1;
         return;
       }
     }
   };
+  // A chunk by one bulk copy from the pre-split pool (thread 0 issues it)
+  auto bulk_a = [&](float* buf, int64_t poff, int kc, int b) {
+    if (tid == 0) {
+      const uint32_t bytes = 2u * kAElems * 4u;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&lbar[b])), "r"(bytes)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(buf)),
+          "l"(pool + poff + (int64_t)kc * 2 * kAElems), "r"(bytes), "r"(smem_u32(&lbar[b]))
+          : "memory");
+    }
+  };
+  bool bulk[2] = {false, false};  // does stage b's A come from a bulk copy
   ChunkRegs regs;
   {
     const float2 *M, *X;
     int kc;
-    chunk_src(0, M, X, kc);
-    load_chunk(regs, M, X, d, g.st[leg], leg == 2, base, nvalid, kc);
-    store_chunk(tsm, regs, leg == 2);
+    int64_t poff;
+    chunk_src(0, M, X, kc, poff);
+    bulk[0] = poff >= 0;
+    if (bulk[0]) bulk_a(tsm, poff, kc, 0);
+    load_chunk(regs, M, X, d, g.st[leg], leg == 2, base, nvalid, kc, !bulk[0]);
+    store_chunk(tsm, regs, leg == 2, !bulk[0]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -242,6 +288,10 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
     const int b = ci & 1;
     float* buf = tsm + b * kStageFloats;
     // make the staged operands visible to the tensor core, then issue
+    if (bulk[b] && ok) {
+      ok = mbar_wait(&lbar[b], lph[b], deadline);
+      lph[b] ^= 1u;
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -266,14 +316,17 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
     if (ci + 1 < nchunks) {
       const float2 *M, *X;
       int kc;
-      chunk_src(ci + 1, M, X, kc);
-      load_chunk(regs, M, X, d, g.st[leg], leg == 2, base, nvalid, kc);
+      int64_t poff;
+      chunk_src(ci + 1, M, X, kc, poff);
+      bulk[b ^ 1] = poff >= 0;
+      load_chunk(regs, M, X, d, g.st[leg], leg == 2, base, nvalid, kc, !bulk[b ^ 1]);
       // the other stage is free once the MMAs of chunk ci-1 have completed
       if (ci >= 1 && ok) {
         ok = mbar_wait(&mbar[b ^ 1], ph[b ^ 1], deadline);
         ph[b ^ 1] ^= 1u;
       }
-      store_chunk(tsm + (b ^ 1) * kStageFloats, regs, leg == 2);
+      if (bulk[b ^ 1] && ok) bulk_a(tsm + (b ^ 1) * kStageFloats, poff, kc, b ^ 1);
+      store_chunk(tsm + (b ^ 1) * kStageFloats, regs, leg == 2, !bulk[b ^ 1]);
     }
   }
   // all MMAs done once the last commit has landed (they complete in order)
@@ -383,7 +436,8 @@ __global__ void k_tc_epilogue(DevTables T, ApList L, Epi ep, const float2* acc) 
 }  // namespace
 
 bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const ApOut* outs_host,
-                     const ApTerm* terms_host, float2* acc, int* flag, cudaStream_t s) {
+                     const ApTerm* terms_host, float2* acc, int* flag, const float* pool, const int64_t* pool_off,
+                     cudaStream_t s) {
   if (L.n_tiles <= 0) return true;
   const bool rk = e.mode != EPI_STORE;
   if (rk && (L.out_end - L.out_begin != 1 || !acc)) return false;
@@ -406,9 +460,21 @@ bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const Ap
     attr = true;
   }
   for (int l = 0; l < 3; ++l)
-    if (has[l]) k_tc_apply<<<tiles[l], kTcThreads, kTcSmem, s>>>(T, L, l, rk ? acc : nullptr, flag);
+    if (has[l])
+      k_tc_apply<<<tiles[l], kTcThreads, kTcSmem, s>>>(T, L, l, rk ? acc : nullptr, flag, pool, pool_off);
   if (rk || ident) k_tc_epilogue<<<L.n_tiles, 32, 0, s>>>(T, L, e, acc);
   return true;
+}
+
+int64_t tc_pool_floats(int d) { return d > kTcM / 2 ? 0 : (int64_t)((2 * d + kTcK - 1) / kTcK) * 2 * kAElems; }
+
+void launch_tc_embed(void* const* mats32, const TcEmbedJob* jobs, int n, float* pool, cudaStream_t s) {
+  for (int i0 = 0; i0 < n; i0 += kTcEmbedBatch) {
+    TcEmbedBatch b{};
+    b.n = std::min(kTcEmbedBatch, n - i0);
+    for (int i = 0; i < b.n; ++i) b.job[i] = jobs[i0 + i];
+    k_tc_embed<<<dim3(b.n, (kTcM + kTcK - 1) / kTcK), kTcThreads, 0, s>>>(mats32, b, pool);
+  }
 }
 
 bool tc_applicable(const ApList& L, const ApOut* outs_host, const ApTerm* terms_host) {
