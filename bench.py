@@ -165,6 +165,43 @@ def timed_steps(torch, g, w, K, flush):
     return total  # ms
 
 
+def rank64_leg(args, pkg, torch, flush, local_rank, forms=(("fp64", 0), ("mixed_fp32", 1))):
+    """The 7-site chain at bond rank 64 in the FP64 and mixed forms: steps/s,
+    per-class kernel time and the mixed-vs-FP64 RDM difference."""
+    w64 = W.exciton_chain(rank=64)
+    k64 = max(2, min(args.steps, 5))
+    res = {}
+    rhos = {}
+    for label, prec in forms:
+        gg = make_gpu(pkg, w64, local_rank, precision=prec)
+        if not args.no_autotune:
+            gg.ttn_autotune(2)
+        gg.ttn_step(w64.dt, 1, 1)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        gg.ttn_stats_reset()
+        ms64 = timed_steps(torch, gg, w64, k64, flush)
+        fl64 = gg.ttn_stats(0)[1]
+        gg.ttn_stats_reset()
+        gg.ttn_profile(True)
+        timed_steps(torch, gg, w64, 1, flush)
+        gg.ttn_profile(False)
+        pr = {k: (gg.ttn_stats(k)[1], gg.ttn_profile_read(k)) for k in range(4)}
+        rhos[label] = gg.ttn_rdm()
+        res[label] = {"steps_per_s": k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64,
+                      "node_contraction_gflop_per_step": fl64 / k64 / 1e9,
+                      "node_contraction_tflops_kernel": pr[0][0] / (pr[0][1] * 1e-3) / 1e12 if pr[0][1] > 0 else None,
+                      "kernel_ms_per_step": {n_: pr[k][1] for k, n_ in
+                                             enumerate(("k_apply", "environment", "qr", "other"))}}
+        gg.close()
+    out = {"workload": "7-site exciton chain as above at bond rank 64 (state 1.97 M complex, nodes 64x64x64)",
+           "steps_timed": k64, **res}
+    if "fp64" in res and "mixed_fp32" in res:
+        out["mixed_speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / res["mixed_fp32"]["ms_per_step"]
+        out["rdm_max_abs_mixed_vs_fp64_gpu"] = float(np.max(np.abs(rhos["fp64"] - rhos["mixed_fp32"])))
+        out["steps_compared"] = 1 + k64 + 1
+    return out
+
+
 def bench_ours(args, rank, world, local_rank):
     import torch
     import paper_2603_17711_gb300 as pkg
@@ -175,6 +212,11 @@ def bench_ours(args, rank, world, local_rank):
         import torch.distributed as dist
     w = workload()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    if args.rank64_only:  # profiling aid: only the rank-64 leg, in the form asked for
+        forms = (("fp64", 0),) if args.rank64_only == "fp64" else (("mixed_fp32", pkg.TTN_MIXED_FP32),)
+        if rank == 0:
+            print(json.dumps({"precision_rank64": rank64_leg(args, pkg, torch, flush, local_rank, forms)}), flush=True)
+        return
 
     # ---- device-timed steps (value) ----
     g = make_gpu(pkg, w, local_rank)
@@ -243,38 +285,7 @@ def bench_ours(args, rank, world, local_rank):
     gb.close()
 
     # ---- precision workload: the same chain at bond rank 64 (QRs up to 4096 x 64) ----
-    r64 = None
-    if not args.no_rank64:
-        w64 = W.exciton_chain(rank=64)
-        k64 = max(2, min(args.steps, 5))
-        res = {}
-        rhos = {}
-        for label, prec in (("fp64", 0), ("mixed_fp32", pkg.TTN_MIXED_FP32)):
-            gg = make_gpu(pkg, w64, local_rank, precision=prec)
-            if not args.no_autotune:
-                gg.ttn_autotune(2)
-            gg.ttn_step(w64.dt, 1, 1)  # warm-up (graph capture)
-            torch.cuda.synchronize()
-            gg.ttn_stats_reset()
-            ms64 = timed_steps(torch, gg, w64, k64, flush)
-            fl64 = gg.ttn_stats(0)[1]
-            gg.ttn_stats_reset()
-            gg.ttn_profile(True)
-            timed_steps(torch, gg, w64, 1, flush)
-            gg.ttn_profile(False)
-            pr = {k: (gg.ttn_stats(k)[1], gg.ttn_profile_read(k)) for k in range(4)}
-            rhos[label] = gg.ttn_rdm()
-            res[label] = {"steps_per_s": k64 / (ms64 * 1e-3), "ms_per_step": ms64 / k64,
-                          "node_contraction_gflop_per_step": fl64 / k64 / 1e9,
-                          "node_contraction_tflops_kernel": pr[0][0] / (pr[0][1] * 1e-3) / 1e12 if pr[0][1] > 0 else None,
-                          "kernel_ms_per_step": {n_: pr[k][1] for k, n_ in
-                                                 enumerate(("k_apply", "environment", "qr", "other"))}}
-            gg.close()
-        r64 = {"workload": "7-site exciton chain as above at bond rank 64 (state 1.97 M complex, nodes 64x64x64)",
-               "steps_timed": k64, **res,
-               "mixed_speedup_vs_fp64": res["fp64"]["ms_per_step"] / res["mixed_fp32"]["ms_per_step"],
-               "rdm_max_abs_mixed_vs_fp64_gpu": float(np.max(np.abs(rhos["fp64"] - rhos["mixed_fp32"]))),
-               "steps_compared": 1 + k64 + 1}
+    r64 = None if args.no_rank64 else rank64_leg(args, pkg, torch, flush, local_rank)
 
     # ---- batched: 256 uneven spin-boson instances in one graph launch per step ----
     batch_out = None
@@ -423,6 +434,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-rank64", action="store_true", help="skip the rank-64 precision leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
+    ap.add_argument("--rank64-only", choices=["fp64", "mixed"], default=None,
+                    help="profiling aid: run only the rank-64 leg in one form (prints that object, not the bench line)")
     ap.add_argument("--batch", type=int, default=256, help="instances in the batched leg")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -317,7 +317,13 @@ struct Exec {
     store(1, E.classes);
     if (E.project >= 0) {
       const PjList& L = p.pj_lists[E.project];
-      run(1, L.flops, [&] { launch_project(h->prec, h->Tlo, L, s); });
+      // wide bonds: the tiled kernel (all classes of one edge share U and its dims)
+      const PjOut& q = p.pj_outs[L.out_begin];
+      const int dq = q.leg == 0 ? q.d0 : q.leg == 1 ? q.d1 : q.d2;
+      const int64_t nrest = (int64_t)q.d0 * q.d1 * q.d2 / dq;
+      run(1, L.flops, [&] {
+        if (!launch_project_tiled(h->prec, h->Tlo, L, dq, nrest, p.sm_count, s)) launch_project(h->prec, h->Tlo, L, s);
+      });
       if (h->tc_pool_on) {
         const int d = p.dims[a][p.tree.leg_index(a, b)];  // current rank of the bond
         std::vector<TcEmbedJob> jobs;

@@ -339,6 +339,126 @@ __global__ void __launch_bounds__(32 * kPjWarps, 4) k_project(DevTables T, PjLis
   ((V*)T.mats[pj.dst_mat])[e] = acc;
 }
 
+// Projection of wide bonds (d >= 32, reduction range >= 1024): 32 x 32 output
+// tiles, reduction range in chunks of 32 staged through shared memory with
+// coalesced loads (along the reduction index, or along the leg when the leg
+// is the contiguous one), 2 x 2 outputs per thread. The range is split over
+// KS CTAs of one cluster, whose partial tiles CTA 0 adds in rank order
+// through distributed shared memory, so results are reproducible.
+constexpr int kPtT = 32;  // output tile edge
+constexpr int kPtR = 32;  // reduction chunk
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_project_tiled(DevTables T, PjList L, int ntx, int KS) {
+  using C = Cx<R>;
+  using V = typename C::T;
+  extern __shared__ __align__(16) unsigned char psm[];
+  V(*Us)[kPtR + 1] = (V(*)[kPtR + 1])psm;
+  V(*Ws)[kPtR + 1] = Us + kPtT;
+  V* slot = (V*)(Ws + kPtT);  // CTA 0: [KS-1][kPtT * kPtT] partial tiles of the other ranks
+  __shared__ int64_t base[kPtR];
+  const int tid = threadIdx.x;
+  const int rank = blockIdx.x % KS, item = blockIdx.x / KS;
+  const int per_out = ntx * ntx;
+  const int o = L.out_begin + item / per_out, tt = item % per_out;
+  const PjOut pj = T.pjs[o];
+  const int dd[3] = {pj.d0, pj.d1, pj.d2};
+  const int64_t st[3] = {(int64_t)pj.d1 * pj.d2, pj.d2, 1};
+  const int l = pj.leg, d = dd[l];
+  const int la = l == 0 ? 1 : 0, lb = l == 2 ? 1 : 2;
+  const int nrest = dd[la] * dd[lb];
+  const int X0 = (tt / ntx) * kPtT, Y0 = (tt % ntx) * kPtT;  // rows x' (conjugated side), columns x
+  const V* __restrict__ U = (const V*)T.bufs[pj.u_buf];
+  const V* __restrict__ W = (const V*)T.bufs[pj.w_buf];
+  const int nch = (nrest + kPtR - 1) / kPtR;
+  const int c0 = (int)((int64_t)rank * nch / KS), c1 = (int)((int64_t)(rank + 1) * nch / KS);
+  const bool leg_fast = l == 2;  // the leg index is the contiguous one
+  const int ty = (tid >> 4) * 2, tx = (tid & 15) * 2;
+  V acc[2][2] = {{C::zero(), C::zero()}, {C::zero(), C::zero()}};
+  for (int c = c0; c < c1; ++c) {
+    const int r0 = c * kPtR;
+    if (tid < kPtR) {
+      const int r = r0 + tid;
+      base[tid] = r < nrest ? (int64_t)(r / dd[lb]) * st[la] + (int64_t)(r % dd[lb]) * st[lb] : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < (kPtT * kPtR) / 256; ++q) {
+      const int e = tid + q * 256;
+      const int row = leg_fast ? (e & 31) : (e >> 5), rr = leg_fast ? (e >> 5) : (e & 31);
+      const bool rin = r0 + rr < nrest;
+      const int xu = X0 + row, xw = Y0 + row;
+      Us[row][rr] = (xu < d && rin) ? U[(int64_t)xu * st[l] + base[rr]] : C::zero();
+      Ws[row][rr] = (xw < d && rin) ? W[(int64_t)xw * st[l] + base[rr]] : C::zero();
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < kPtR; ++rr) {
+      const V u0 = Us[ty][rr], u1 = Us[ty + 1][rr], w0 = Ws[tx][rr], w1 = Ws[tx + 1][rr];
+      acc[0][0] = C::fmaj(u0, w0, acc[0][0]);
+      acc[0][1] = C::fmaj(u0, w1, acc[0][1]);
+      acc[1][0] = C::fmaj(u1, w0, acc[1][0]);
+      acc[1][1] = C::fmaj(u1, w1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  if (KS > 1) {
+    cg::cluster_group cluster = cg::this_cluster();
+    if (rank > 0) {
+      V* dst = cluster.map_shared_rank(slot, 0) + (size_t)(rank - 1) * kPtT * kPtT;
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) dst[(ty + i) * kPtT + tx + j] = acc[i][j];
+    }
+    cluster.sync();
+    if (rank > 0) return;
+    for (int r = 1; r < KS; ++r)
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) acc[i][j] = C::add(acc[i][j], slot[(size_t)(r - 1) * kPtT * kPtT + (ty + i) * kPtT + tx + j]);
+  }
+  V* E = (V*)T.mats[pj.dst_mat];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      const int xp = X0 + ty + i, x = Y0 + tx + j;
+      if (xp < d && x < d) E[xp * d + x] = acc[i][j];
+    }
+}
+
+bool launch_project_tiled(int prec, const DevTables& T, const PjList& L, int d, int64_t nrest, int sm_count,
+                          cudaStream_t s) {
+  const int n_outs = L.out_end - L.out_begin;
+  // FP64 projections are bound by FP64 issue either way and measured faster
+  // on the per-entry kernel (rank-64 env update 100 vs 117 ms/step)
+  if (prec != PREC_F32 || n_outs <= 0 || d < 32 || nrest < 1024) return false;
+  const int ntx = (d + kPtT - 1) / kPtT;
+  const int items = n_outs * ntx * ntx;
+  const int nch = (int)((nrest + kPtR - 1) / kPtR);
+  const int kmax = prec == PREC_F32 ? 8 : 4;
+  int KS = 1;
+  while (KS < kmax && KS < nch && items * KS < 2 * sm_count) ++KS;
+  const size_t vb = prec == PREC_F32 ? sizeof(float2) : sizeof(double2);
+  const size_t smem = vb * (2 * kPtT * (kPtR + 1) + (size_t)(KS - 1) * kPtT * kPtT);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_project_tiled<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(k_project_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(items * KS), 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr1[1];
+  attr1[0].id = cudaLaunchAttributeClusterDimension;
+  attr1[0].val.clusterDim.x = (unsigned)KS;
+  attr1[0].val.clusterDim.y = 1;
+  attr1[0].val.clusterDim.z = 1;
+  cfg.attrs = attr1;
+  cfg.numAttrs = 1;
+  if (prec == PREC_F32) return cudaLaunchKernelEx(&cfg, k_project_tiled<float>, T, L, ntx, KS) == cudaSuccess;
+  return cudaLaunchKernelEx(&cfg, k_project_tiled<double>, T, L, ntx, KS) == cudaSuccess;
+}
+
 void launch_project(int prec, const DevTables& T, const PjList& L, cudaStream_t s) {
   if (L.n_tiles <= 0) return;
   if (prec == PREC_F32)

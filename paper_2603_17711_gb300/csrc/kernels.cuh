@@ -79,6 +79,13 @@ struct TcEmbedBatch {
 int64_t tc_pool_floats(int d);
 void launch_tc_embed(void* const* mats32, const TcEmbedJob* jobs, int n, float* pool, cudaStream_t s);
 void launch_project(int prec, const DevTables& T, const PjList& L, cudaStream_t s);
+// The same projections for wide bonds in the FP32 form (every output d x d
+// with d >= 32 and a reduction range of >= 1024 positions, all outputs of the
+// list alike):
+// shared-memory tiled, range split over a cluster. Returns false (nothing
+// launched) when the list does not qualify or the launch fails.
+bool launch_project_tiled(int prec, const DevTables& T, const PjList& L, int d, int64_t nrest, int sm_count,
+                          cudaStream_t s);
 // Householder QR of node tensor U (dims d[3]) matricised toward leg `leg`.
 // U is overwritten with Q (same layout), R (d_leg x d_leg, row-major) written to R.
 // work: >= P complex, qbuf: >= P complex. A non-finite ||U||_F sets *flag and
