@@ -12,8 +12,10 @@
 // out of the reverse accumulation by itself. Every reduction runs in a fixed
 // order (row blocks summed in block order), so results are reproducible.
 //
-// The trailing and Q updates are spread over ceil(rows / kRB) CTAs, i.e. over
-// the whole GPU for a 4096-row matrix; only the panels run on one cluster.
+// The trailing and Q updates are spread over one CTA per SM (rows split evenly,
+// at most kRB per CTA): they are bound by the FP64 issue rate of each SM, so
+// an even split over all SMs is what shortens them. Only the panels run on
+// one cluster.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -22,9 +24,18 @@ namespace ttn {
 
 namespace {
 
-constexpr int kRB = 32;                // rows per CTA of the update kernels
+constexpr int kRB = 32;                // most rows per CTA of the update kernels
 constexpr int kNB = kQrPanelMaxNb;     // panel width
 constexpr int kGatherMax = 1024;       // CTAs of the gather / norm partials
+constexpr int kBlkCap = 256;           // most CTAs of a balanced row partition
+
+// The update kernels are bound by the SM's FP64 issue rate, so the rows are
+// split into one block per SM (at most kRB rows each, at least one row).
+int rows_per_block(int64_t rows, int sms) {
+  const int64_t s = std::max(1, std::min(sms, kBlkCap));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kRB, (rows + s - 1) / s));
+}
+int64_t max_blocks(int64_t m) { return std::max<int64_t>(kBlkCap, (m + kRB - 1) / kRB); }
 
 int64_t round16(int64_t x) { return (x + 15) / 16 * 16; }
 
@@ -48,7 +59,7 @@ QbLayout qb_layout(int64_t m, int64_t n) {
   L.phase = take(n);
   L.skip = take((n + 3) / 4);
   L.T = take((n + kNB - 1) / kNB * kNB * kNB);
-  L.Y = take((m + kRB - 1) / kRB * kNB * n);
+  L.Y = take(max_blocks(m) * kNB * n);
   L.Z = take(kNB * n);
   L.total = o;
   return L;
@@ -115,23 +126,24 @@ __global__ void k_qb_norm(const double* part, int np, double tol, double* sc, in
   }
 }
 
-// Ypart[b][i][k] = sum over rows r of block b (rows from c0) with r >= c0+i of
-// conj(V[r][c0+i]) * S[r][k], for i < nb and k0 <= k < n. V = column block of A.
+// Ypart[b][i][k] = sum over rows r of block b (rows from c0, rbs rows per
+// block) with r >= c0+i of conj(V[r][c0+i]) * S[r][k], for i < nb and
+// k0 <= k < n. V = column block of A.
 __global__ void __launch_bounds__(256) k_qb_ypart(const double2* A, const double2* S, int64_t m, int c0, int nb,
-                                                  int k0, int n, double2* Ypart, const double* sc) {
+                                                  int k0, int n, int rbs, double2* Ypart, const double* sc) {
   __shared__ double2 Vs[kNB][kRB];
   __shared__ double2 Ss[kRB][kQrClusterMaxN + 1];
   if (aborted(sc)) return;
   const int b = blockIdx.x;
-  const int64_t rb = c0 + (int64_t)b * kRB;
+  const int64_t rb = c0 + (int64_t)b * rbs;
   const int nk = n - k0;
-  for (int t = threadIdx.x; t < nb * kRB; t += blockDim.x) {
-    const int i = t / kRB, rr = t % kRB;
+  for (int t = threadIdx.x; t < nb * rbs; t += blockDim.x) {
+    const int i = t / rbs, rr = t % rbs;
     const int64_t r = rb + rr;
     Vs[i][rr] = (r < m && r >= c0 + i) ? A[(int64_t)(c0 + i) * m + r] : make_double2(0.0, 0.0);
   }
-  for (int t = threadIdx.x; t < nk * kRB; t += blockDim.x) {
-    const int kk = t / kRB, rr = t % kRB;
+  for (int t = threadIdx.x; t < nk * rbs; t += blockDim.x) {
+    const int kk = t / rbs, rr = t % rbs;
     const int64_t r = rb + rr;
     Ss[rr][kk] = r < m ? S[(int64_t)(k0 + kk) * m + r] : make_double2(0.0, 0.0);
   }
@@ -139,8 +151,8 @@ __global__ void __launch_bounds__(256) k_qb_ypart(const double2* A, const double
   for (int t = threadIdx.x; t < nb * nk; t += blockDim.x) {
     const int i = t / nk, kk = t % nk;
     double2 y = make_double2(0.0, 0.0);
-#pragma unroll 8
-    for (int rr = 0; rr < kRB; ++rr) y = cfmaj(Vs[i][rr], Ss[rr][kk], y);
+#pragma unroll 4
+    for (int rr = 0; rr < rbs; ++rr) y = cfmaj(Vs[i][rr], Ss[rr][kk], y);
     Ypart[((int64_t)b * kNB + i) * n + k0 + kk] = y;
   }
 }
@@ -150,7 +162,12 @@ __global__ void __launch_bounds__(256) k_qb_ypart(const double2* A, const double
 __global__ void __launch_bounds__(256) k_qb_zsum(const double2* Ypart, int nblk, int nb, int k0, int n,
                                                  const double2* T, int trans, double2* Z, const double* sc) {
   __shared__ double2 y[kNB];
+  __shared__ double2 Ts[kNB * kNB];  // T'[i][j], loaded while the block sums run
   if (aborted(sc)) return;
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int i = t / nb, j = t % nb;
+    Ts[t] = trans ? make_double2(T[j * nb + i].x, -T[j * nb + i].y) : T[t];
+  }
   const int k = k0 + blockIdx.x;
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int w = threadIdx.x >> 5; w < nb; w += nw) {  // warp-uniform
@@ -168,24 +185,22 @@ __global__ void __launch_bounds__(256) k_qb_zsum(const double2* Ypart, int nblk,
   if ((int)threadIdx.x < nb) {
     const int i = threadIdx.x;
     double2 z = make_double2(0.0, 0.0);
-    for (int j = 0; j < nb; ++j) {
-      const double2 t = trans ? make_double2(T[j * nb + i].x, -T[j * nb + i].y) : T[i * nb + j];
-      z = cfma(t, y[j], z);
-    }
+    for (int j = 0; j < nb; ++j) z = cfma(Ts[i * nb + j], y[j], z);
     Z[(int64_t)i * n + k] = z;
   }
 }
 
-// D[r][k] -= sum_i V[r][c0+i] Z[i][k] for the rows of block b and k0 <= k < n.
+// D[r][k] -= sum_i V[r][c0+i] Z[i][k] for the rows of block b (rbs rows per
+// block) and k0 <= k < n.
 __global__ void __launch_bounds__(256) k_qb_update(const double2* A, double2* D, int64_t m, int c0, int nb, int k0,
-                                                   int n, const double2* Z, const double* sc) {
+                                                   int n, int rbs, const double2* Z, const double* sc) {
   __shared__ double2 Vs[kNB][kRB];
   __shared__ double2 Zs[kNB][kQrClusterMaxN];
   if (aborted(sc)) return;
-  const int64_t rb = c0 + (int64_t)blockIdx.x * kRB;
+  const int64_t rb = c0 + (int64_t)blockIdx.x * rbs;
   const int nk = n - k0;
-  for (int t = threadIdx.x; t < nb * kRB; t += blockDim.x) {
-    const int i = t / kRB, rr = t % kRB;
+  for (int t = threadIdx.x; t < nb * rbs; t += blockDim.x) {
+    const int i = t / rbs, rr = t % rbs;
     const int64_t r = rb + rr;
     Vs[i][rr] = (r < m && r >= c0 + i) ? A[(int64_t)(c0 + i) * m + r] : make_double2(0.0, 0.0);
   }
@@ -194,8 +209,8 @@ __global__ void __launch_bounds__(256) k_qb_update(const double2* A, double2* D,
     Zs[i][kk] = Z[(int64_t)i * n + k0 + kk];
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < nk * kRB; t += blockDim.x) {
-    const int kk = t / kRB, rr = t % kRB;
+  for (int t = threadIdx.x; t < nk * rbs; t += blockDim.x) {
+    const int kk = t / rbs, rr = t % rbs;
     const int64_t r = rb + rr;
     if (r >= m) continue;
     double2* d = D + (int64_t)(k0 + kk) * m + r;
@@ -273,6 +288,12 @@ bool launch_qr_blocked(double2* U, int d0, int d1, int d2, int leg, double tol, 
   double2* Z = work + L.Z;
   double2* X = qbuf;
 
+  static int sms = 0;  // SMs of the device (the update kernels use one CTA per SM)
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 1;
+  }
   const int g1 = (int)std::min<int64_t>(kGatherMax, (m * n + 255) / 256);
   k_qb_gather<<<g1, 256, 0, s>>>(U, d0, d1, d2, leg, A, m, n, part);
   k_qb_norm<<<1, 32, 0, s>>>(part, g1, tol, sc, flag);
@@ -283,10 +304,11 @@ bool launch_qr_blocked(double2* U, int d0, int d1, int d2, int leg, double tol, 
     if (!launch_qr_panel(pn, s)) return false;
     const int k0 = c0 + nb;
     if (k0 >= n) break;
-    const int nblk = (int)((m - c0 + kRB - 1) / kRB);
-    k_qb_ypart<<<nblk, 256, 0, s>>>(A, A, m, c0, nb, k0, n, Y, sc);
+    const int rbs = rows_per_block(m - c0, sms);
+    const int nblk = (int)((m - c0 + rbs - 1) / rbs);
+    k_qb_ypart<<<nblk, 256, 0, s>>>(A, A, m, c0, nb, k0, n, rbs, Y, sc);
     k_qb_zsum<<<n - k0, 256, 0, s>>>(Y, nblk, nb, k0, n, pn.T, 1, Z, sc);
-    k_qb_update<<<nblk, 256, 0, s>>>(A, A, m, c0, nb, k0, n, Z, sc);
+    k_qb_update<<<nblk, 256, 0, s>>>(A, A, m, c0, nb, k0, n, rbs, Z, sc);
   }
   // Q = H_0 .. H_{n-1} [I_n; 0], panels applied last to first
   const int gi = (int)std::min<int64_t>(2048, (m * n + 255) / 256);
@@ -294,10 +316,11 @@ bool launch_qr_blocked(double2* U, int d0, int d1, int d2, int leg, double tol, 
   for (int c0 = (n - 1) / kNB * kNB; c0 >= 0; c0 -= kNB) {
     const int nb = std::min(kNB, n - c0);
     const double2* Tp = T + (int64_t)(c0 / kNB) * kNB * kNB;
-    const int nblk = (int)((m - c0 + kRB - 1) / kRB);
-    k_qb_ypart<<<nblk, 256, 0, s>>>(A, X, m, c0, nb, c0, n, Y, sc);
+    const int rbs = rows_per_block(m - c0, sms);
+    const int nblk = (int)((m - c0 + rbs - 1) / rbs);
+    k_qb_ypart<<<nblk, 256, 0, s>>>(A, X, m, c0, nb, c0, n, rbs, Y, sc);
     k_qb_zsum<<<n - c0, 256, 0, s>>>(Y, nblk, nb, c0, n, Tp, 0, Z, sc);
-    k_qb_update<<<nblk, 256, 0, s>>>(A, X, m, c0, nb, c0, n, Z, sc);
+    k_qb_update<<<nblk, 256, 0, s>>>(A, X, m, c0, nb, c0, n, rbs, Z, sc);
   }
   k_qb_finish<<<gi, 256, 0, s>>>(A, X, m, n, alpha, phase, skip, U, d0, d1, d2, leg, R, U_lo, R_lo, sc);
   return true;
