@@ -53,6 +53,7 @@ struct ttn_ctx {
   double2* qr_work = nullptr;
   int64_t qr_elems = 0;
   float2* tc_acc = nullptr;  // FP32 scratch of the tensor-core path (mixed form)
+  int64_t tc_acc_elems = 0;  // its capacity: three node-sized leg planes
   // pre-split operator matrices of the tensor-core path: on when some job list
   // was tensor-core eligible at bind time; every writer of those matrices
   // then refreshes their pool copies
@@ -247,7 +248,7 @@ Layout layout_of(const Plan& p, int prec) {
     // ys, T_g, W_c and the bond shadow / stage input in FP32
     L.scratch32 = take(((int64_t)(2 + p.buf.n_t + p.buf.n_w) * S + 3 * r2 + 3 * p.theta_cap) * sizeof(float2));
     L.bufs_tab_lo = take(p.buf.n_bufs * sizeof(void*));
-    L.tc_acc = take(S * sizeof(float2));
+    L.tc_acc = take(3 * S * sizeof(float2));
     // pre-split copies of the operator matrices the job lists use (not the bond matrix)
     L.tc_off_host.assign(p.mats.size(), -1);
     std::vector<char> used(p.mats.size(), 0);
@@ -301,7 +302,7 @@ struct Exec {
     if (h->prec == PREC_F32 && h->params.tensor_cores && h->tc_acc &&
         tc_applicable(L, p.ap_outs.data(), p.ap_terms.data())) {
       run(kind, L.flops, [&] {
-        if (!launch_apply_tc(h->Tlo, L, e, p.ap_outs.data(), p.ap_terms.data(), h->tc_acc, h->flag_dev,
+        if (!launch_apply_tc(h->Tlo, L, e, p.ap_outs.data(), p.ap_terms.data(), h->tc_acc, h->tc_acc_elems, h->flag_dev,
                              h->tc_pool_on ? h->tc_pool : nullptr, h->tc_pool_on ? h->tc_off_dev : nullptr, s))
           launch_apply(h->prec, h->Tlo, L, e, s);
       });
@@ -1004,6 +1005,7 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
         h->h_mats_lo[i] = p.mats[i].off >= 0 ? (void*)(p32 + p.mats[i].off) : nullptr;
       h->h_mats_lo[p.bond_mat] = h->h_bufs_lo[p.buf.bond_y];
       h->tc_acc = (float2*)(base + L.tc_acc);
+      h->tc_acc_elems = 3 * S;
       h->tc_pool = (float*)(base + L.tc_pool);
       h->tc_off_dev = (int64_t*)(base + L.tc_off);
       h->tc_off = L.tc_off_host;

@@ -54,15 +54,16 @@ void launch_apply(int prec, const DevTables& T, const ApList& L, const Epi& e, c
 
 // Mixed form: the same list with its mode products on the tcgen05 tensor
 // cores (tc_apply.cu, 3xTF32). outs_host/terms_host: host copies of the job
-// tables; acc: FP32 scratch of the largest output (RK epilogue lists); flag
-// bit 3 on a timed-out MMA wait. tc_applicable: 3-leg outputs, contracted
+// tables; acc: FP32 scratch of acc_elems complex values (RK epilogue lists;
+// one-output lists run their three legs in one launch when 3 planes of the
+// output fit); flag bit 3 on a timed-out MMA wait. tc_applicable: 3-leg outputs, contracted
 // legs of dimension <= 64, largest output >= 16384 elements.
 // pool/pool_off (nullable): pre-split operator matrices (launch_tc_embed),
 // pool_off[mat] the float offset of a matrix or -1 (staged by the threads).
 bool tc_applicable(const ApList& L, const ApOut* outs_host, const ApTerm* terms_host);
 bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const ApOut* outs_host,
-                     const ApTerm* terms_host, float2* acc, int* flag, const float* pool, const int64_t* pool_off,
-                     cudaStream_t s);
+                     const ApTerm* terms_host, float2* acc, int64_t acc_elems, int* flag, const float* pool,
+                     const int64_t* pool_off, cudaStream_t s);
 // Pre-split copies of FP32 operator matrices for the tensor-core path: for
 // each job, matrix `mat` (d x d, d <= 64) of the FP32 matrix table is embedded
 // and split into tf32 hi / lo in the layout the apply kernel stages, at float

@@ -172,28 +172,44 @@ __global__ void k_tc_embed(void* const* mats32, TcEmbedBatch jb, float* pool) {
   store_chunk(out, r, false, true, false);  // the A hi / lo halves only
 }
 
-// One CTA = one (output, 64-position tile) of leg `leg`: Y_o (+)= sum over the
-// output's terms on this leg of M_t x_leg X_t. Y_o is the STORE destination
-// (or acc for an RK epilogue list); the first leg with terms writes, later
-// legs add. Flag bit 3 on a timed-out MMA wait.
-__global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, int leg, float2* acc, int* flag,
-                                                        const float* pool, const int64_t* pool_off) {
+// One CTA = one (output, 64-position tile) of one leg: Y_o (+)= sum over the
+// output's terms on this leg of M_t x_leg X_t.
+//  * leg >= 0 (lists of several outputs): every CTA works on `leg`; Y_o is the
+//    STORE destination, the first leg with terms writes, later legs add
+//    (separate launches in leg order).
+//  * leg < 0 (lists of one output): the legs run in one launch, CTAs
+//    [lt[l], lt[l+1]) on leg l, each writing its own plane part + l*pstride;
+//    the epilogue adds the planes in leg order.
+// Flag bit 3 on a timed-out MMA wait.
+constexpr int kTcMaxTerms = 64;  // terms of one leg held in shared memory
+__global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, int leg, int4 lt, float2* part,
+                                                        int64_t pstride, int* flag, const float* pool,
+                                                        const int64_t* pool_off) {
   extern __shared__ __align__(128) float tsm[];
   __shared__ __align__(8) uint64_t mbar[2], lbar[2];  // MMA commits, bulk A copies
   __shared__ uint32_t tmem_base;
   __shared__ int64_t base[kTcN];
+  __shared__ int s_terms[kTcMaxTerms];  // this leg's terms, in list order
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool planes = leg < 0;
   // locate the output and tile of this CTA
   int o = L.out_begin, tile = blockIdx.x;
   int64_t rest = 0;
-  for (;; ++o) {
-    if (o >= L.out_end) return;
+  if (planes) {
+    leg = (int)blockIdx.x >= lt.z ? 2 : (int)blockIdx.x >= lt.y ? 1 : 0;
+    tile = (int)blockIdx.x - (leg == 0 ? lt.x : leg == 1 ? lt.y : lt.z);
     const ApOut& u = T.outs[o];
-    const int dl = leg == 0 ? u.d0 : leg == 1 ? u.d1 : u.d2;
-    rest = (int64_t)u.d0 * u.d1 * u.d2 / dl;
-    const int nt = (int)((rest + kTcN - 1) / kTcN);
-    if (tile < nt) break;
-    tile -= nt;
+    rest = (int64_t)u.d0 * u.d1 * u.d2 / (leg == 0 ? u.d0 : leg == 1 ? u.d1 : u.d2);
+  } else {
+    for (;; ++o) {
+      if (o >= L.out_end) return;
+      const ApOut& u = T.outs[o];
+      const int dl = leg == 0 ? u.d0 : leg == 1 ? u.d1 : u.d2;
+      rest = (int64_t)u.d0 * u.d1 * u.d2 / dl;
+      const int nt = (int)((rest + kTcN - 1) / kTcN);
+      if (tile < nt) break;
+      tile -= nt;
+    }
   }
   const ApOut out = T.outs[o];
   const Geo3 g = geo_of(out);
@@ -202,9 +218,13 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
   for (int t = out.term_begin; t < out.term_end; ++t) {
     const ApTerm tm = T.terms[t];
     if (tm.mat < 0) continue;
-    if (tm.leg == leg) ++n_here;
+    if (tm.leg == leg) {
+      if (tid == 0 && n_here < kTcMaxTerms) s_terms[n_here] = t;
+      ++n_here;
+    }
     if (tm.leg < leg) earlier = true;
   }
+  if (planes) earlier = false;  // own plane
   if (n_here == 0) return;  // uniform over the CTA
   const int d = g.d[leg];
   const int nkc = (2 * d + kTcK - 1) / kTcK;
@@ -219,7 +239,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
     }
   }
   __syncthreads();
-  float2* Y = L.out_end - L.out_begin == 1 && acc ? acc : (float2*)T.bufs[out.dst];
+  float2* Y = part ? part + (int64_t)leg * pstride : (float2*)T.bufs[out.dst];
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
@@ -239,21 +259,27 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
   bool ok = true;
   uint32_t ph[2] = {0u, 0u}, lph[2] = {0u, 0u};
 
-  // chunk ci -> (term, kc)
   // chunk ci -> (operator, tensor, K chunk); poff: pre-split operator offset or -1
   auto chunk_src = [&](int ci, const float2*& M, const float2*& X, int& kc, int64_t& poff) {
     int k = ci / nkc;
     kc = ci % nkc;
-    for (int t = out.term_begin; t < out.term_end; ++t) {
-      const ApTerm tm = T.terms[t];
-      if (tm.mat < 0 || tm.leg != leg) continue;
-      if (k-- == 0) {
-        M = (const float2*)T.mats[tm.mat];
-        X = (const float2*)T.bufs[tm.src];
-        poff = pool_off ? pool_off[tm.mat] : -1;
-        return;
+    int tt = -1;
+    if (n_here <= kTcMaxTerms) {
+      tt = s_terms[k];
+    } else {
+      for (int t = out.term_begin; t < out.term_end; ++t) {
+        const ApTerm tm = T.terms[t];
+        if (tm.mat < 0 || tm.leg != leg) continue;
+        if (k-- == 0) {
+          tt = t;
+          break;
+        }
       }
     }
+    const ApTerm tm = T.terms[tt];
+    M = (const float2*)T.mats[tm.mat];
+    X = (const float2*)T.bufs[tm.src];
+    poff = pool_off ? pool_off[tm.mat] : -1;
   };
   // A chunk by one bulk copy from the pre-split pool (thread 0 issues it)
   auto bulk_a = [&](float* buf, int64_t poff, int kc, int b) {
@@ -374,8 +400,10 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
 
 // Identity terms and the epilogue (RK4 stage update or nothing) of a list
 // whose mode products ran on the tensor cores: the tiles of the apply kernel
-// (32 elements), one thread per element.
-__global__ void k_tc_epilogue(DevTables T, ApList L, Epi ep, const float2* acc) {
+// (32 elements), one thread per element. legs != 0 (one-output lists): the
+// mode products are in the planes acc + l*pstride of the legs l in the mask,
+// added here in leg order; otherwise in acc (RK) or the destination (store).
+__global__ void k_tc_epilogue(DevTables T, ApList L, Epi ep, const float2* acc, int legs, int64_t pstride) {
   const int tile = blockIdx.x;
   int o = L.out_begin;
   while (o + 1 < L.out_end && T.outs[o + 1].tile0 <= tile) ++o;
@@ -398,7 +426,23 @@ __global__ void k_tc_epilogue(DevTables T, ApList L, Epi ep, const float2* acc) 
   const bool rk = ep.mode != EPI_STORE;
   float2* Y = rk ? const_cast<float2*>(acc) : (float2*)T.bufs[out.dst];
   if (any) {
-    const float2 y = Y[e];
+    float2 y = make_float2(0.f, 0.f);
+    if (legs) {
+      bool first = true;
+      for (int l = 0; l < 3; ++l) {
+        if (!(legs >> l & 1)) continue;
+        const float2 v = acc[(int64_t)l * pstride + e];
+        if (first) {
+          y = v;
+        } else {  // same order and operands as the adds of the leg-by-leg launches
+          y.x = v.x + y.x;
+          y.y = v.y + y.y;
+        }
+        first = false;
+      }
+    } else {
+      y = Y[e];
+    }
     s.x += y.x;
     s.y += y.y;
   }
@@ -436,17 +480,20 @@ __global__ void k_tc_epilogue(DevTables T, ApList L, Epi ep, const float2* acc) 
 }  // namespace
 
 bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const ApOut* outs_host,
-                     const ApTerm* terms_host, float2* acc, int* flag, const float* pool, const int64_t* pool_off,
-                     cudaStream_t s) {
+                     const ApTerm* terms_host, float2* acc, int64_t acc_elems, int* flag, const float* pool,
+                     const int64_t* pool_off, cudaStream_t s) {
   if (L.n_tiles <= 0) return true;
   const bool rk = e.mode != EPI_STORE;
-  if (rk && (L.out_end - L.out_begin != 1 || !acc)) return false;
+  const bool one = L.out_end - L.out_begin == 1;
+  if (rk && (!one || !acc)) return false;
   int tiles[3] = {0, 0, 0};
   bool has[3] = {false, false, false}, ident = false;
+  int64_t P = 0;
   for (int o = L.out_begin; o < L.out_end; ++o) {
     const ApOut& u = outs_host[o];
     const int dd[3] = {u.d0, u.d1, u.d2};
-    for (int l = 0; l < 3; ++l) tiles[l] += (int)(((int64_t)u.d0 * u.d1 * u.d2 / dd[l] + kTcN - 1) / kTcN);
+    P = (int64_t)u.d0 * u.d1 * u.d2;
+    for (int l = 0; l < 3; ++l) tiles[l] += (int)((P / dd[l] + kTcN - 1) / kTcN);
     for (int t = u.term_begin; t < u.term_end; ++t) {
       if (terms_host[t].mat < 0)
         ident = true;
@@ -459,10 +506,25 @@ bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const Ap
     cudaFuncSetAttribute(k_tc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     attr = true;
   }
+  // one output whose leg planes fit the scratch: all legs in one launch
+  if (one && acc && 3 * P <= acc_elems) {
+    int4 lt;
+    lt.x = 0;
+    lt.y = lt.x + (has[0] ? tiles[0] : 0);
+    lt.z = lt.y + (has[1] ? tiles[1] : 0);
+    lt.w = lt.z + (has[2] ? tiles[2] : 0);
+    const int legs = (has[0] ? 1 : 0) | (has[1] ? 2 : 0) | (has[2] ? 4 : 0);
+    if (lt.w > 0) k_tc_apply<<<lt.w, kTcThreads, kTcSmem, s>>>(T, L, -1, lt, acc, P, flag, pool, pool_off);
+    k_tc_epilogue<<<L.n_tiles, 32, 0, s>>>(T, L, e, acc, legs, P);
+    return true;
+  }
+  const int4 none = make_int4(0, 0, 0, 0);
   for (int l = 0; l < 3; ++l)
-    if (has[l])
-      k_tc_apply<<<tiles[l], kTcThreads, kTcSmem, s>>>(T, L, l, rk ? acc : nullptr, flag, pool, pool_off);
-  if (rk || ident) k_tc_epilogue<<<L.n_tiles, 32, 0, s>>>(T, L, e, acc);
+    if (has[l]) {
+      float2* part = rk ? acc : nullptr;  // RK lists: the single output's sum goes to acc
+      k_tc_apply<<<tiles[l], kTcThreads, kTcSmem, s>>>(T, L, l, none, part, 0, flag, pool, pool_off);
+    }
+  if (rk || ident) k_tc_epilogue<<<L.n_tiles, 32, 0, s>>>(T, L, e, acc, 0, 0);
   return true;
 }
 
