@@ -192,37 +192,92 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
   __shared__ int s_terms[kTcMaxTerms];  // this leg's terms, in list order
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool planes = leg < 0;
-  // locate the output and tile of this CTA
+  // The job tables are read with parallel loads (one L2 round trip each
+  // instead of one per output and per term): locate the output and tile of
+  // this CTA, then list this leg's terms with their operands.
+  __shared__ int s_o, s_tile, s_n, s_earlier;
+  __shared__ ApTerm s_all[kTcMaxTerms];
+  __shared__ const float2* s_M[kTcMaxTerms];
+  __shared__ const float2* s_X[kTcMaxTerms];
+  __shared__ int64_t s_poff[kTcMaxTerms];
   int o = L.out_begin, tile = blockIdx.x;
-  int64_t rest = 0;
   if (planes) {
     leg = (int)blockIdx.x >= lt.z ? 2 : (int)blockIdx.x >= lt.y ? 1 : 0;
     tile = (int)blockIdx.x - (leg == 0 ? lt.x : leg == 1 ? lt.y : lt.z);
-    const ApOut& u = T.outs[o];
-    rest = (int64_t)u.d0 * u.d1 * u.d2 / (leg == 0 ? u.d0 : leg == 1 ? u.d1 : u.d2);
   } else {
-    for (;; ++o) {
-      if (o >= L.out_end) return;
-      const ApOut& u = T.outs[o];
-      const int dl = leg == 0 ? u.d0 : leg == 1 ? u.d1 : u.d2;
-      rest = (int64_t)u.d0 * u.d1 * u.d2 / dl;
-      const int nt = (int)((rest + kTcN - 1) / kTcN);
-      if (tile < nt) break;
-      tile -= nt;
+    if (warp == 0) {
+      int found = -1, left = tile;
+      for (int o0 = L.out_begin; o0 < L.out_end && found < 0; o0 += 32) {
+        int nt = 0;
+        if (o0 + lane < L.out_end) {
+          const ApOut u = T.outs[o0 + lane];
+          const int dl = leg == 0 ? u.d0 : leg == 1 ? u.d1 : u.d2;
+          nt = (int)(((int64_t)u.d0 * u.d1 * u.d2 / dl + kTcN - 1) / kTcN);
+        }
+        int inc = nt;  // inclusive prefix sum over the lanes
+        for (int k = 1; k < 32; k <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, inc, k);
+          if (lane >= k) inc += v;
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, left < inc);
+        if (hit) {
+          const int fl = __ffs(hit) - 1;
+          found = o0 + fl;
+          left -= __shfl_sync(0xffffffffu, inc - nt, fl);
+        } else {
+          left -= __shfl_sync(0xffffffffu, inc, 31);
+        }
+      }
+      if (lane == 0) {
+        s_o = found;
+        s_tile = left;
+      }
     }
+    __syncthreads();
+    if (s_o < 0) return;  // uniform: past the last tile
+    o = s_o;
+    tile = s_tile;
   }
   const ApOut out = T.outs[o];
   const Geo3 g = geo_of(out);
+  const int64_t rest = (int64_t)out.d0 * out.d1 * out.d2 / g.d[leg];
+  const int n_all = out.term_end - out.term_begin;
   int n_here = 0;
   bool earlier = false;
-  for (int t = out.term_begin; t < out.term_end; ++t) {
-    const ApTerm tm = T.terms[t];
-    if (tm.mat < 0) continue;
-    if (tm.leg == leg) {
-      if (tid == 0 && n_here < kTcMaxTerms) s_terms[n_here] = t;
-      ++n_here;
+  if (n_all <= kTcMaxTerms) {
+    if (tid < n_all) s_all[tid] = T.terms[out.term_begin + tid];
+    __syncthreads();
+    if (tid == 0) {
+      int n = 0, e = 0;
+      for (int t = 0; t < n_all; ++t) {
+        const ApTerm tm = s_all[t];
+        if (tm.mat < 0) continue;
+        if (tm.leg == leg) s_terms[n++] = out.term_begin + t;
+        if (tm.leg < leg) e = 1;
+      }
+      s_n = n;
+      s_earlier = e;
     }
-    if (tm.leg < leg) earlier = true;
+    __syncthreads();
+    n_here = s_n;
+    earlier = s_earlier != 0;
+  } else {
+    for (int t = out.term_begin; t < out.term_end; ++t) {
+      const ApTerm tm = T.terms[t];
+      if (tm.mat < 0) continue;
+      if (tm.leg == leg) {
+        if (tid == 0 && n_here < kTcMaxTerms) s_terms[n_here] = t;
+        ++n_here;
+      }
+      if (tm.leg < leg) earlier = true;
+    }
+  }
+  __syncthreads();  // s_terms complete (both paths)
+  if (tid < n_here && tid < kTcMaxTerms) {
+    const ApTerm tm = T.terms[s_terms[tid]];
+    s_M[tid] = (const float2*)T.mats[tm.mat];
+    s_X[tid] = (const float2*)T.bufs[tm.src];
+    s_poff[tid] = pool_off ? pool_off[tm.mat] : -1;
   }
   if (planes) earlier = false;  // own plane
   if (n_here == 0) return;  // uniform over the CTA
@@ -265,7 +320,10 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
     kc = ci % nkc;
     int tt = -1;
     if (n_here <= kTcMaxTerms) {
-      tt = s_terms[k];
+      M = s_M[k];
+      X = s_X[k];
+      poff = s_poff[k];
+      return;
     } else {
       for (int t = out.term_begin; t < out.term_end; ++t) {
         const ApTerm tm = T.terms[t];
@@ -294,23 +352,34 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
           : "memory");
     }
   };
-  bool bulk[2] = {false, false};  // does stage b's A come from a bulk copy
-  ChunkRegs regs;
-  {
+  // Chunk ci is staged in stage ci & 1. Its tensor operand is loaded into
+  // registers two iterations ahead (two register sets), so a chunk's loads
+  // overlap the MMAs of the two chunks before it.
+  bool bulk[2] = {false, false};  // does the A of the chunk of slot ci & 1 come from a bulk copy
+  int64_t poffs[2] = {-1, -1};
+  int kcs[2] = {0, 0};
+  ChunkRegs R0, R1;
+  auto fetch = [&](int ci, ChunkRegs& R) {
     const float2 *M, *X;
     int kc;
     int64_t poff;
-    chunk_src(0, M, X, kc, poff);
-    bulk[0] = poff >= 0;
-    if (bulk[0]) bulk_a(tsm, poff, kc, 0);
-    load_chunk(regs, M, X, d, g.st[leg], leg == 2, base, nvalid, kc, !bulk[0]);
-    store_chunk(tsm, regs, leg == 2, !bulk[0]);
-  }
+    chunk_src(ci, M, X, kc, poff);
+    bulk[ci & 1] = poff >= 0;
+    poffs[ci & 1] = poff;
+    kcs[ci & 1] = kc;
+    load_chunk(R, M, X, d, g.st[leg], leg == 2, base, nvalid, kc, !bulk[ci & 1]);
+  };
+  fetch(0, R0);
+  if (bulk[0]) bulk_a(tsm, poffs[0], kcs[0], 0);
+  store_chunk(tsm, R0, leg == 2, !bulk[0]);
+  if (nchunks > 1) fetch(1, R1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  for (int ci = 0; ci < nchunks; ++ci) {
+  // one iteration: MMAs of chunk ci; loads of chunk ci+2 into Rld; chunk ci+1
+  // (in Rst since the previous iteration) stored into the other stage
+  auto step = [&](int ci, ChunkRegs& Rst, ChunkRegs& Rld) {
     const int b = ci & 1;
     float* buf = tsm + b * kStageFloats;
     // make the staged operands visible to the tensor core, then issue
@@ -339,21 +408,20 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
                        smem_u32(&mbar[b]))
                    : "memory");
     }
+    if (ci + 2 < nchunks) fetch(ci + 2, Rld);
     if (ci + 1 < nchunks) {
-      const float2 *M, *X;
-      int kc;
-      int64_t poff;
-      chunk_src(ci + 1, M, X, kc, poff);
-      bulk[b ^ 1] = poff >= 0;
-      load_chunk(regs, M, X, d, g.st[leg], leg == 2, base, nvalid, kc, !bulk[b ^ 1]);
       // the other stage is free once the MMAs of chunk ci-1 have completed
       if (ci >= 1 && ok) {
         ok = mbar_wait(&mbar[b ^ 1], ph[b ^ 1], deadline);
         ph[b ^ 1] ^= 1u;
       }
-      if (bulk[b ^ 1] && ok) bulk_a(tsm + (b ^ 1) * kStageFloats, poff, kc, b ^ 1);
-      store_chunk(tsm + (b ^ 1) * kStageFloats, regs, leg == 2, !bulk[b ^ 1]);
+      if (bulk[b ^ 1] && ok) bulk_a(tsm + (b ^ 1) * kStageFloats, poffs[b ^ 1], kcs[b ^ 1], b ^ 1);
+      store_chunk(tsm + (b ^ 1) * kStageFloats, Rst, leg == 2, !bulk[b ^ 1]);
     }
+  };
+  for (int ci = 0; ci < nchunks; ci += 2) {
+    step(ci, R1, R0);
+    if (ci + 1 < nchunks) step(ci + 1, R0, R1);
   }
   // all MMAs done once the last commit has landed (they complete in order)
   if (ok) ok = mbar_wait(&mbar[(nchunks - 1) & 1], ph[(nchunks - 1) & 1], deadline);
