@@ -646,39 +646,47 @@ void launch_copy(double2* dst, float2* dst_lo, const double2* src, int64_t n, cu
 // Reduced density matrix (rho_S = <0|Omega>): contraction of one node with
 // the vectors of its two child legs (the n = 0 unit vector on open legs).
 // ---------------------------------------------------------------------------
-__global__ void k_rdm_node(const double2* U, int d0, int d1, int d2, int root, const double2* w1,
-                           const double2* w2, double2* out) {
+// One CTA per output; warp w takes the rows b = w, w + 8, ... of the output's
+// slice (for the root: one row, the output itself), the lanes split the row
+// over c and a fixed butterfly adds them, and the warps' sums are added in warp
+// order, so the result is reproducible.
+__global__ void __launch_bounds__(256) k_rdm_node(const double2* U, int d0, int d1, int d2, int root,
+                                                  const double2* w1, const double2* w2, double2* out) {
   // root: out[i*d1 + j] = sum_c U[i, j, c] w2[c]; else out[a] = sum_{b,c} U[a,b,c] w1[b] w2[c]
-  const int nout = root ? d0 * d1 : d0;
-  for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < nout; e += blockDim.x * gridDim.x) {
-    double2 acc = make_double2(0.0, 0.0);
-    if (root) {
-      const double2* row = U + (int64_t)e * d2;
-      if (w2) {
-        for (int c = 0; c < d2; ++c) acc = cfma(row[c], w2[c], acc);
-      } else {
-        acc = row[0];
+  __shared__ double2 part[8];
+  const int e = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nrow = root ? 1 : (w1 ? d1 : 1);
+  const double2* blk = U + (int64_t)e * (root ? d2 : (int64_t)d1 * d2);
+  double2 acc = make_double2(0.0, 0.0);
+  for (int b = warp; b < nrow; b += 8) {
+    const double2* row = blk + (int64_t)b * d2;
+    double2 inner = make_double2(0.0, 0.0);
+    if (w2) {
+      for (int c = lane; c < d2; c += 32) inner = cfma(row[c], w2[c], inner);
+      for (int o = 16; o > 0; o >>= 1) {
+        inner.x += __shfl_xor_sync(0xffffffffu, inner.x, o);
+        inner.y += __shfl_xor_sync(0xffffffffu, inner.y, o);
       }
     } else {
-      const double2* blk = U + (int64_t)e * d1 * d2;
-      for (int b = 0; b < (w1 ? d1 : 1); ++b) {
-        double2 inner = make_double2(0.0, 0.0);
-        const double2* row = blk + (int64_t)b * d2;
-        if (w2) {
-          for (int c = 0; c < d2; ++c) inner = cfma(row[c], w2[c], inner);
-        } else {
-          inner = row[0];
-        }
-        acc = w1 ? cfma(w1[b], inner, acc) : inner;
-      }
+      inner = row[0];
     }
-    out[e] = acc;
+    acc = (!root && w1) ? cfma(w1[b], inner, acc) : inner;
+  }
+  if (lane == 0) part[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = part[0];
+    for (int w = 1; w < 8 && w < nrow; ++w) {
+      t.x += part[w].x;
+      t.y += part[w].y;
+    }
+    out[e] = t;
   }
 }
 void launch_rdm_node(const double2* U, int d0, int d1, int d2, bool root, const double2* w1,
                      const double2* w2, double2* out, cudaStream_t s) {
   const int nout = root ? d0 * d1 : d0;
-  k_rdm_node<<<(nout + 127) / 128, 128, 0, s>>>(U, d0, d1, d2, root ? 1 : 0, w1, w2, out);
+  if (nout > 0) k_rdm_node<<<nout, 256, 0, s>>>(U, d0, d1, d2, root ? 1 : 0, w1, w2, out);
 }
 
 __global__ void k_drive(double2* const* mats, float2* const* mats32, const DriveMat* list, int n, DriveArgs g) {
