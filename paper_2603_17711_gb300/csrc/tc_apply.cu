@@ -40,6 +40,14 @@ constexpr int kBElems = kTcN * kTcK;
 constexpr int kStageFloats = 2 * kAElems + 2 * kBElems;
 constexpr size_t kTcSmem = 2 * kStageFloats * sizeof(float);  // 96 KB
 constexpr int64_t kTcMinElems = 16384;  // smaller lists stay on the CUDA cores
+constexpr int kTcMaxSplit = 8;          // most parts a leg's terms are cut into
+
+// CTA ranges, term parts and first plane of each leg of a one-output launch
+struct TcLegs {
+  int lt[4];  // leg l: CTAs [lt[l], lt[l+1]), ks[l] parts x its tiles
+  int ks[3];
+  int pb[3];
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint64_t gtimer() {
@@ -178,11 +186,12 @@ __global__ void k_tc_embed(void* const* mats32, TcEmbedBatch jb, float* pool) {
 //    STORE destination, the first leg with terms writes, later legs add
 //    (separate launches in leg order).
 //  * leg < 0 (lists of one output): the legs run in one launch, CTAs
-//    [lt[l], lt[l+1]) on leg l, each writing its own plane part + l*pstride;
-//    the epilogue adds the planes in leg order.
+//    [lg.lt[l], lg.lt[l+1]) on leg l; leg l's terms are cut into lg.ks[l]
+//    contiguous parts, part j of a tile writing its own plane
+//    part + (lg.pb[l] + j) * pstride; the epilogue adds the planes in order.
 // Flag bit 3 on a timed-out MMA wait.
 constexpr int kTcMaxTerms = 64;  // terms of one leg held in shared memory
-__global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, int leg, int4 lt, float2* part,
+__global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, int leg, TcLegs lg, float2* part,
                                                         int64_t pstride, int* flag, const float* pool,
                                                         const int64_t* pool_off) {
   extern __shared__ __align__(128) float tsm[];
@@ -201,9 +210,14 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
   __shared__ const float2* s_X[kTcMaxTerms];
   __shared__ int64_t s_poff[kTcMaxTerms];
   int o = L.out_begin, tile = blockIdx.x;
+  int split = 0, nsplit = 1;
   if (planes) {
-    leg = (int)blockIdx.x >= lt.z ? 2 : (int)blockIdx.x >= lt.y ? 1 : 0;
-    tile = (int)blockIdx.x - (leg == 0 ? lt.x : leg == 1 ? lt.y : lt.z);
+    const int bx = (int)blockIdx.x;
+    leg = bx >= lg.lt[2] ? 2 : bx >= lg.lt[1] ? 1 : 0;
+    nsplit = lg.ks[leg];
+    const int ntile = (lg.lt[leg + 1] - lg.lt[leg]) / nsplit;
+    split = (bx - lg.lt[leg]) / ntile;
+    tile = (bx - lg.lt[leg]) % ntile;
   } else {
     if (warp == 0) {
       int found = -1, left = tile;
@@ -283,7 +297,10 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
   if (n_here == 0) return;  // uniform over the CTA
   const int d = g.d[leg];
   const int nkc = (2 * d + kTcK - 1) / kTcK;
-  const int nchunks = n_here * nkc;
+  // this CTA's part of the leg's terms: [k_begin, k_begin + n_mine)
+  const int k_begin = split * n_here / nsplit;
+  const int n_mine = (split + 1) * n_here / nsplit - k_begin;
+  const int nchunks = n_mine * nkc;
   const int64_t n0 = (int64_t)tile * kTcN;
   const int nvalid = rest - n0 < kTcN ? (int)(rest - n0) : kTcN;
   {
@@ -294,7 +311,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
     }
   }
   __syncthreads();
-  float2* Y = part ? part + (int64_t)leg * pstride : (float2*)T.bufs[out.dst];
+  float2* Y = part ? part + (planes ? (int64_t)(lg.pb[leg] + split) * pstride : 0) : (float2*)T.bufs[out.dst];
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
@@ -316,7 +333,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
 
   // chunk ci -> (operator, tensor, K chunk); poff: pre-split operator offset or -1
   auto chunk_src = [&](int ci, const float2*& M, const float2*& X, int& kc, int64_t& poff) {
-    int k = ci / nkc;
+    int k = k_begin + ci / nkc;
     kc = ci % nkc;
     int tt = -1;
     if (n_here <= kTcMaxTerms) {
@@ -468,10 +485,11 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
 
 // Identity terms and the epilogue (RK4 stage update or nothing) of a list
 // whose mode products ran on the tensor cores: the tiles of the apply kernel
-// (32 elements), one thread per element. legs != 0 (one-output lists): the
-// mode products are in the planes acc + l*pstride of the legs l in the mask,
-// added here in leg order; otherwise in acc (RK) or the destination (store).
-__global__ void k_tc_epilogue(DevTables T, ApList L, Epi ep, const float2* acc, int legs, int64_t pstride) {
+// (32 elements), one thread per element. nplanes > 0 (one-output lists): the
+// mode products are in the planes acc + q*pstride, q < nplanes, added here in
+// plane order (leg by leg, each leg's term parts in order); otherwise in acc
+// (RK) or the destination (store).
+__global__ void k_tc_epilogue(DevTables T, ApList L, Epi ep, const float2* acc, int nplanes, int64_t pstride) {
   const int tile = blockIdx.x;
   int o = L.out_begin;
   while (o + 1 < L.out_end && T.outs[o + 1].tile0 <= tile) ++o;
@@ -495,18 +513,12 @@ __global__ void k_tc_epilogue(DevTables T, ApList L, Epi ep, const float2* acc, 
   float2* Y = rk ? const_cast<float2*>(acc) : (float2*)T.bufs[out.dst];
   if (any) {
     float2 y = make_float2(0.f, 0.f);
-    if (legs) {
-      bool first = true;
-      for (int l = 0; l < 3; ++l) {
-        if (!(legs >> l & 1)) continue;
-        const float2 v = acc[(int64_t)l * pstride + e];
-        if (first) {
-          y = v;
-        } else {  // same order and operands as the adds of the leg-by-leg launches
-          y.x = v.x + y.x;
-          y.y = v.y + y.y;
-        }
-        first = false;
+    if (nplanes > 0) {
+      y = acc[e];
+      for (int q = 1; q < nplanes; ++q) {  // same order and operands as the adds of leg-by-leg launches
+        const float2 v = acc[(int64_t)q * pstride + e];
+        y.x = v.x + y.x;
+        y.y = v.y + y.y;
       }
     } else {
       y = Y[e];
@@ -574,19 +586,61 @@ bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const Ap
     cudaFuncSetAttribute(k_tc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     attr = true;
   }
-  // one output whose leg planes fit the scratch: all legs in one launch
+  // one output whose leg planes fit the scratch: all legs in one launch, a
+  // leg's terms cut into parts while that shortens the longest per-CTA chain
+  // and the launch stays within about two CTAs per SM
   if (one && acc && 3 * P <= acc_elems) {
-    int4 lt;
-    lt.x = 0;
-    lt.y = lt.x + (has[0] ? tiles[0] : 0);
-    lt.z = lt.y + (has[1] ? tiles[1] : 0);
-    lt.w = lt.z + (has[2] ? tiles[2] : 0);
-    const int legs = (has[0] ? 1 : 0) | (has[1] ? 2 : 0) | (has[2] ? 4 : 0);
-    if (lt.w > 0) k_tc_apply<<<lt.w, kTcThreads, kTcSmem, s>>>(T, L, -1, lt, acc, P, flag, pool, pool_off);
-    k_tc_epilogue<<<L.n_tiles, 32, 0, s>>>(T, L, e, acc, legs, P);
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 1;
+    }
+    const ApOut& u = outs_host[L.out_begin];
+    const int dd[3] = {u.d0, u.d1, u.d2};
+    int nterm[3] = {0, 0, 0};
+    for (int t = u.term_begin; t < u.term_end; ++t)
+      if (terms_host[t].mat >= 0) ++nterm[terms_host[t].leg];
+    TcLegs lg{};
+    int ctas = 0, planes = 0;
+    for (int l = 0; l < 3; ++l) {
+      lg.ks[l] = 1;
+      if (has[l]) {
+        ctas += tiles[l];
+        ++planes;
+      }
+    }
+    for (;;) {
+      int best = -1;
+      int64_t chain = 0;
+      for (int l = 0; l < 3; ++l) {
+        if (!has[l]) continue;
+        const int64_t c = (int64_t)((nterm[l] + lg.ks[l] - 1) / lg.ks[l]) * ((2 * dd[l] + kTcK - 1) / kTcK);
+        if (c > chain) {
+          chain = c;
+          best = l;
+        }
+      }
+      if (best < 0 || lg.ks[best] >= std::min(nterm[best], kTcMaxSplit)) break;
+      if (ctas + tiles[best] > 2 * sms || (int64_t)(planes + 1) * P > acc_elems) break;
+      ++lg.ks[best];
+      ctas += tiles[best];
+      ++planes;
+    }
+    int q = 0;
+    lg.lt[0] = 0;
+    for (int l = 0; l < 3; ++l) {
+      lg.pb[l] = q;
+      const int n = has[l] ? tiles[l] * lg.ks[l] : 0;
+      lg.lt[l + 1] = lg.lt[l] + n;
+      if (has[l]) q += lg.ks[l];
+    }
+    if (lg.lt[3] > 0) k_tc_apply<<<lg.lt[3], kTcThreads, kTcSmem, s>>>(T, L, -1, lg, acc, P, flag, pool, pool_off);
+    k_tc_epilogue<<<L.n_tiles, 32, 0, s>>>(T, L, e, acc, q, P);
     return true;
   }
-  const int4 none = make_int4(0, 0, 0, 0);
+  const TcLegs none{};
   for (int l = 0; l < 3; ++l)
     if (has[l]) {
       float2* part = rk ? acc : nullptr;  // RK lists: the single output's sum goes to acc
