@@ -28,6 +28,9 @@ constexpr int kRB = 32;                // most rows per CTA of the update kernel
 constexpr int kNB = kQrPanelMaxNb;     // panel width
 constexpr int kGatherMax = 1024;       // CTAs of the gather / norm partials
 constexpr int kBlkCap = 256;           // most CTAs of a balanced row partition
+constexpr int kNpair = kNB * (kNB - 1) / 2;  // strictly-upper Gram entries of a panel
+constexpr int kPgRows = 64;            // most panel rows per CTA of the grid panel kernel
+constexpr int kMaxPanels = (kQrClusterMaxN + kNB - 1) / kNB;
 
 // The update kernels are bound by the SM's FP64 issue rate, so the rows are
 // split into one block per SM (at most kRB rows each, at least one row).
@@ -41,7 +44,7 @@ int64_t round16(int64_t x) { return (x + 15) / 16 * 16; }
 
 // Offsets (complex elements) of the blocked-QR scratch inside `work`.
 struct QbLayout {
-  int64_t A, part, sc, beta, alpha, phase, skip, T, Y, Z, total;
+  int64_t A, part, sc, beta, alpha, phase, skip, T, Y, Z, rec, own, gp, gf, bar, total;
 };
 QbLayout qb_layout(int64_t m, int64_t n) {
   QbLayout L;
@@ -61,6 +64,11 @@ QbLayout qb_layout(int64_t m, int64_t n) {
   L.T = take((n + kNB - 1) / kNB * kNB * kNB);
   L.Y = take(max_blocks(m) * kNB * n);
   L.Z = take(kNB * n);
+  L.rec = take((int64_t)kNB * kBlkCap * kNB);
+  L.own = take(kNB * kNB);
+  L.gp = take((int64_t)kBlkCap * kNpair);
+  L.gf = take(kNpair);
+  L.bar = take(kMaxPanels / 4 + 1);  // one 32-bit grid-barrier counter per panel
   L.total = o;
   return L;
 }
@@ -77,6 +85,13 @@ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {  // a
   c.x = fma(-a.y, b.y, c.x);
   c.y = fma(a.x, b.y, c.y);
   c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {  // c - a*b
+  c.x = fma(-a.x, b.x, c.x);
+  c.x = fma(a.y, b.y, c.x);
+  c.y = fma(-a.x, b.y, c.y);
+  c.y = fma(-a.y, b.x, c.y);
   return c;
 }
 __device__ __forceinline__ double wsum(double v) {
@@ -110,8 +125,10 @@ __global__ void __launch_bounds__(256) k_qb_gather(const double2* U, int d0, int
   }
 }
 
-// sc[0] = tol * ||A||_F (NaN and flag bit 1 when the norm is not finite)
-__global__ void k_qb_norm(const double* part, int np, double tol, double* sc, int* flag) {
+// sc[0] = tol * ||A||_F (NaN and flag bit 1 when the norm is not finite);
+// the panels' grid-barrier counters start at zero
+__global__ void k_qb_norm(const double* part, int np, double tol, double* sc, int* flag, unsigned* bar) {
+  if (threadIdx.x < kMaxPanels) bar[threadIdx.x] = 0u;
   double t = 0.0;
   for (int i = threadIdx.x; i < np; i += 32) t += part[i];
   t = wsum(t);
@@ -224,6 +241,221 @@ __global__ void __launch_bounds__(256) k_qb_update(const double2* A, double2* D,
   }
 }
 
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Grid barrier of a cooperative launch: every CTA adds one to *bar, then
+// (if wait) waits until it reaches target. The wait is bounded by the
+// kernel-wide deadline; on expiry bit 2 of *flag is set and false returned.
+__device__ bool grid_arrive_wait(unsigned* bar, unsigned target, bool wait, uint64_t deadline, int* flag) {
+  __shared__ int s_ok;
+  __syncthreads();  // the CTA's writes before the barrier ...
+  if (threadIdx.x == 0) {
+    __threadfence();  // ... ordered before the arrival
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    if (wait) {
+      while (*(volatile unsigned*)bar < target)
+        if (gtimer() > deadline) {
+          atomicOr(flag, 2);
+          ok = 0;
+          break;
+        }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Panel factorisation over the whole GPU (cooperative launch, G <= SMs CTAs):
+// the rows [c0, m) of the nb panel columns are split over the CTAs (rp <=
+// kPgRows each, kept in shared memory) and column j costs one grid barrier.
+// Before it every CTA writes its record rec[j][cta] = (|x_j|^2 over its rows,
+// u_k = x_j^H a_k for k > j) and the owner of row j writes own[j] = (x_0,
+// a_k[j]); after it every CTA adds the G records in the same fixed order, so
+// all CTAs hold bitwise the same alpha, phi, beta and w_k = sum u_k + alpha
+// conj(phi) a_k[j], and updates its own rows. Convention, skipping rule and
+// outputs are those of the cluster kernel in panel mode: v below the diagonal
+// and R entries above written back to A, per-column beta / alpha / phase /
+// skip, and the panel's WY factor T from T^{-1} = diag(1/beta) +
+// strictly-upper(V^H V) (partial Grams reduced over the grid, back substitution
+// in CTA 0). Every wait is bounded (2 s): bit 2 of *flag on expiry.
+__global__ void __launch_bounds__(256) k_qb_panel_grid(double2* A, int64_t m, int c0, int nb, const double* sc,
+                                                       double* beta, double* alpha, double2* phase, int* skip,
+                                                       double2* T, double2* rec, double2* own, double2* gp,
+                                                       double2* gf, unsigned* bar, int* flag) {
+  __shared__ double2 X[kNB][kPgRows];  // my rows of the panel, column-major
+  __shared__ double2 red[kNB];         // this column's summed record: [0].x = |x|^2, [t] = sum u_{j+t}
+  __shared__ double2 s_own[kNB];       // [0] = x_0, [t] = a_{j+t}[j]
+  __shared__ double s_beta[kNB], s_alpha[kNB];
+  __shared__ double2 s_phase[kNB], s_gam;
+  __shared__ int s_skip[kNB];
+  __shared__ double2 s_gf[kNpair];
+  if (aborted(sc)) return;  // uniform over the grid
+  const double thr = sc[0];
+  const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int64_t Rrows = m - c0;
+  const int rp = (int)((Rrows + G - 1) / G);
+  const int64_t r0 = (int64_t)me * rp;
+  const int nr = (int)max((int64_t)0, min(Rrows, r0 + rp) - r0);
+  const uint64_t deadline = gtimer() + 2000000000ull;
+  bool alive = true;
+  for (int t = tid; t < nb * rp; t += blockDim.x) {
+    const int c = t / rp, i = t % rp;
+    X[c][i] = i < nr ? A[(int64_t)(c0 + c) * m + c0 + r0 + i] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    const int i0 = (int)max((int64_t)0, (int64_t)j - r0);
+    const bool ownr = j >= r0 && j < r0 + nr;
+    const int lrow = (int)(j - r0);
+    // record of my rows: task 0 = |x_j|^2, task t = u_{j+t}
+    for (int task = wid; task < nb - j; task += 8) {
+      double2 u = make_double2(0.0, 0.0);
+      if (task == 0) {
+        for (int i = i0 + lane; i < nr; i += 32) u.x = fma(X[j][i].x, X[j][i].x, fma(X[j][i].y, X[j][i].y, u.x));
+      } else {
+        const int k = j + task;
+        for (int i = i0 + lane; i < nr; i += 32) u = cfmaj(X[j][i], X[k][i], u);
+      }
+      u.x = wsum(u.x);
+      u.y = wsum(u.y);
+      if (lane == 0) rec[((int64_t)j * kBlkCap + me) * kNB + task] = u;
+    }
+    if (ownr)
+      for (int k = j + tid; k < nb; k += blockDim.x) own[j * kNB + k] = X[k][lrow];
+    if (alive) alive = grid_arrive_wait(bar, (unsigned)((j + 1) * G), true, deadline, flag);
+    {  // sum the G records in a fixed order: 16 threads per task, then a butterfly
+      const int task = tid >> 4, sub = tid & 15;
+      double2 v = make_double2(0.0, 0.0);
+      if (task < nb - j) {
+        double2 a[kBlkCap / 16];
+#pragma unroll
+        for (int q = 0; q < kBlkCap / 16; ++q) {
+          const int c = sub + 16 * q;
+          a[q] = c < G ? __ldcg(&rec[((int64_t)j * kBlkCap + c) * kNB + task]) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int q = 0; q < kBlkCap / 16; ++q) {
+          v.x += a[q].x;
+          v.y += a[q].y;
+        }
+      }
+      for (int o = 8; o > 0; o >>= 1) {  // within each group of 16 lanes
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      }
+      if (sub == 0 && task < nb - j) red[task] = v;
+      if (tid < nb - j) s_own[tid] = __ldcg(&own[j * kNB + j + tid]);
+    }
+    __syncthreads();
+    if (wid == 0) {  // alpha, phi, beta as in the cluster kernel (two lanes share a sqrt and a division)
+      const double a2 = red[0].x;
+      const double2 x0 = s_own[0];
+      const double rt = sqrt(lane == 1 ? fma(x0.x, x0.x, x0.y * x0.y) : a2);
+      const double al = __shfl_sync(0xffffffffu, rt, 0);
+      const double ax0 = __shfl_sync(0xffffffffu, rt, 1);
+      if (!(al > thr)) {
+        if (lane == 0) {
+          s_skip[j] = 1;
+          s_beta[j] = 0.0;
+          s_alpha[j] = 0.0;
+          s_phase[j] = make_double2(1.0, 0.0);
+        }
+      } else {
+        const double rc = 1.0 / (lane == 1 ? al * (al + ax0) : ax0);
+        const double inv = __shfl_sync(0xffffffffu, rc, 0);
+        const double be = __shfl_sync(0xffffffffu, rc, 1);
+        const double2 phi = ax0 > 0.0 ? make_double2(x0.x * inv, x0.y * inv) : make_double2(1.0, 0.0);
+        if (lane == 0) {
+          s_skip[j] = 0;
+          s_beta[j] = be;
+          s_alpha[j] = al;
+          s_phase[j] = make_double2(-phi.x, -phi.y);
+          s_gam = make_double2(al * phi.x, -al * phi.y);
+          if (ownr) X[j][lrow] = make_double2(fma(phi.x, al, x0.x), fma(phi.y, al, x0.y));
+        }
+      }
+    }
+    __syncthreads();
+    if (s_skip[j]) {
+      for (int i = i0 + tid; i < nr; i += blockDim.x) X[j][i] = make_double2(0.0, 0.0);
+    } else {
+      const double be = s_beta[j];
+      const double2 gam = s_gam;
+      const int nk = nb - j - 1, len = nr - i0;
+      for (int t = tid; len > 0 && t < nk * len; t += blockDim.x) {
+        const int k = j + 1 + t / len, i = i0 + t % len;
+        const double2 rj = s_own[k - j];
+        double2 w = red[k - j];
+        w.x = fma(gam.x, rj.x, fma(-gam.y, rj.y, w.x));
+        w.y = fma(gam.x, rj.y, fma(gam.y, rj.x, w.y));
+        const double2 bw = make_double2(be * w.x, be * w.y);
+        X[k][i] = cfms(X[j][i], bw, X[k][i]);
+      }
+    }
+    __syncthreads();
+  }
+  // write back: v below the diagonal, R entries above; per-column scalars
+  for (int t = tid; t < nb * nr; t += blockDim.x) {
+    const int c = t / nr, i = t % nr;
+    A[(int64_t)(c0 + c) * m + c0 + r0 + i] = X[c][i];
+  }
+  if (me == 0)
+    for (int c = tid; c < nb; c += blockDim.x) {
+      beta[c0 + c] = s_beta[c];
+      alpha[c0 + c] = s_alpha[c];
+      phase[c0 + c] = s_phase[c];
+      skip[c0 + c] = s_skip[c];
+    }
+  // partial strictly-upper Gram of my rows (v_a vanishes above row a)
+  const int npair = nb * (nb - 1) / 2;
+  for (int pq = tid; pq < npair; pq += blockDim.x) {
+    int b = 1;
+    while ((b + 1) * b / 2 <= pq) ++b;
+    const int a = pq - b * (b - 1) / 2;
+    double2 g = make_double2(0.0, 0.0);
+    for (int i = (int)max((int64_t)0, (int64_t)b - r0); i < nr; ++i) g = cfmaj(X[a][i], X[b][i], g);
+    gp[(int64_t)me * kNpair + pq] = g;
+  }
+  if (alive) alive = grid_arrive_wait(bar, (unsigned)((nb + 1) * G), true, deadline, flag);
+  // full Gram entry pq (CTA pq mod G, warp 0): the G partials in a fixed order
+  for (int pq = me; pq < npair; pq += G) {
+    if (wid == 0) {
+      double2 g = make_double2(0.0, 0.0);
+      for (int c = lane; c < G; c += 32) {
+        const double2 v = __ldcg(&gp[(int64_t)c * kNpair + pq]);
+        g.x += v.x;
+        g.y += v.y;
+      }
+      g.x = wsum(g.x);
+      g.y = wsum(g.y);
+      if (lane == 0) gf[pq] = g;
+    }
+  }
+  // CTA 0 waits for the whole Gram, then solves T column by column
+  if (alive) alive = grid_arrive_wait(bar, (unsigned)((nb + 2) * G), me == 0, deadline, flag);
+  if (me != 0) return;
+  for (int pq = tid; pq < npair; pq += blockDim.x) s_gf[pq] = __ldcg(&gf[pq]);
+  __syncthreads();
+  for (int c = wid; c < nb; c += 8) {
+    double2 acc = make_double2(lane == c ? 1.0 : 0.0, 0.0);
+    for (int a = c; a >= 0; --a) {
+      const double ba = s_beta[a];
+      double2 ta = make_double2(ba * acc.x, ba * acc.y);
+      ta.x = __shfl_sync(0xffffffffu, ta.x, a);
+      ta.y = __shfl_sync(0xffffffffu, ta.y, a);
+      if (lane == a) T[a * nb + c] = ta;
+      if (lane < a) acc = cfms(s_gf[a * (a - 1) / 2 + lane], ta, acc);
+    }
+    for (int a = c + 1 + lane; a < nb; a += 32) T[a * nb + c] = make_double2(0.0, 0.0);
+  }
+}
+
 __global__ void k_qb_identity(double2* X, int64_t m, int64_t n, const double* sc) {
   if (aborted(sc)) return;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m * n; k += (int64_t)gridDim.x * blockDim.x)
@@ -287,21 +519,45 @@ bool launch_qr_blocked(double2* U, int d0, int d1, int d2, int leg, double tol, 
   double2* Y = work + L.Y;
   double2* Z = work + L.Z;
   double2* X = qbuf;
+  unsigned* bar = (unsigned*)(work + L.bar);
 
-  static int sms = 0;  // SMs of the device (the update kernels use one CTA per SM)
+  static int sms = 0, coop = 0, occ = 0;  // SMs (one CTA each for the FP64-bound kernels), cooperative launch
   if (sms == 0) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       sms = 1;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) coop = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_qb_panel_grid, 256, 0) != cudaSuccess) occ = 0;
   }
+  // a panel over the whole GPU (one grid barrier per column) when the device
+  // guarantees co-residency; else on one cluster
+  auto panel = [&](const QrPanel& pn, int idx) -> bool {
+    const int64_t rows = m - pn.c0;
+    const int G = (int)std::min<int64_t>(std::min(sms, kBlkCap), (rows + 7) / 8);
+    if (coop && occ >= 1 && G >= 1 && (rows + G - 1) / G <= kPgRows) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(G, 1, 1);
+      cfg.blockDim = dim3(256, 1, 1);
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeCooperative;
+      at[0].val.cooperative = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, k_qb_panel_grid, A, (int64_t)m, pn.c0, pn.nb, (const double*)sc, beta, alpha,
+                                phase, skip, pn.T, work + L.rec, work + L.own, work + L.gp, work + L.gf, bar + idx,
+                                flag) == cudaSuccess;
+    }
+    return launch_qr_panel(pn, s);
+  };
   const int g1 = (int)std::min<int64_t>(kGatherMax, (m * n + 255) / 256);
   k_qb_gather<<<g1, 256, 0, s>>>(U, d0, d1, d2, leg, A, m, n, part);
-  k_qb_norm<<<1, 32, 0, s>>>(part, g1, tol, sc, flag);
+  k_qb_norm<<<1, 32, 0, s>>>(part, g1, tol, sc, flag, bar);
   // factorisation: panel, then its reflectors on the trailing columns
   for (int c0 = 0; c0 < n; c0 += kNB) {
     const int nb = std::min(kNB, n - c0);
     QrPanel pn{nullptr, A, (int)m, n, c0, nb, sc, beta, alpha, phase, skip, T + (int64_t)(c0 / kNB) * kNB * kNB};
-    if (!launch_qr_panel(pn, s)) return false;
+    if (!panel(pn, c0 / kNB)) return false;
     const int k0 = c0 + nb;
     if (k0 >= n) break;
     const int rbs = rows_per_block(m - c0, sms);
