@@ -68,7 +68,7 @@ QbLayout qb_layout(int64_t m, int64_t n) {
   L.own = take(kNB * kNB);
   L.gp = take((int64_t)kBlkCap * kNpair);
   L.gf = take(kNpair);
-  L.bar = take(kMaxPanels / 4 + 1);  // one 32-bit grid-barrier counter per panel
+  L.bar = take(kMaxPanels * 8 / 4);  // kBarLanes (8) 32-bit grid-barrier counters per panel
   L.total = o;
   return L;
 }
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) k_qb_gather(const double2* U, int d0, int
 // sc[0] = tol * ||A||_F (NaN and flag bit 1 when the norm is not finite);
 // the panels' grid-barrier counters start at zero
 __global__ void k_qb_norm(const double* part, int np, double tol, double* sc, int* flag, unsigned* bar) {
-  if (threadIdx.x < kMaxPanels) bar[threadIdx.x] = 0u;
+  if (threadIdx.x < kMaxPanels * 8) bar[threadIdx.x] = 0u;
   double t = 0.0;
   for (int i = threadIdx.x; i < np; i += 32) t += part[i];
   t = wsum(t);
@@ -246,26 +246,36 @@ __device__ __forceinline__ uint64_t gtimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Grid barrier of a cooperative launch: every CTA adds one to *bar, then
-// (if wait) waits until it reaches target. The wait is bounded by the
-// kernel-wide deadline; on expiry bit 2 of *flag is set and false returned.
+// Grid barrier of a cooperative launch over kBarLanes counters (CTA c adds
+// one to bar[c % kBarLanes], so the arrivals do not all serialise on one
+// address); a waiting CTA polls the counters with one warp until their sum
+// reaches target. The wait is bounded by the kernel-wide deadline; on expiry
+// bit 2 of *flag is set and false returned.
+constexpr int kBarLanes = 8;
 __device__ bool grid_arrive_wait(unsigned* bar, unsigned target, bool wait, uint64_t deadline, int* flag) {
   __shared__ int s_ok;
   __syncthreads();  // the CTA's writes before the barrier ...
-  if (threadIdx.x == 0) {
-    __threadfence();  // ... ordered before the arrival
-    atomicAdd(bar, 1u);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    if (lane == 0) {
+      __threadfence();  // ... ordered before the arrival
+      atomicAdd(bar + blockIdx.x % kBarLanes, 1u);
+    }
     int ok = 1;
     if (wait) {
-      while (*(volatile unsigned*)bar < target)
-        if (gtimer() > deadline) {
-          atomicOr(flag, 2);
+      for (;;) {
+        unsigned v = lane < kBarLanes ? *(volatile unsigned*)(bar + lane) : 0u;
+        for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (__shfl_sync(0xffffffffu, v, 0) >= target) break;
+        if (__shfl_sync(0xffffffffu, (int)(gtimer() > deadline), 0)) {  // warp-uniform decision
+          if (lane == 0) atomicOr(flag, 2);
           ok = 0;
           break;
         }
+      }
       __threadfence();
     }
-    s_ok = ok;
+    if (lane == 0) s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
@@ -340,10 +350,13 @@ __global__ void __launch_bounds__(256) k_qb_panel_grid(double2* A, int64_t m, in
           a[q] = c < G ? __ldcg(&rec[((int64_t)j * kBlkCap + c) * kNB + task]) : make_double2(0.0, 0.0);
         }
 #pragma unroll
-        for (int q = 0; q < kBlkCap / 16; ++q) {
-          v.x += a[q].x;
-          v.y += a[q].y;
-        }
+        for (int h = kBlkCap / 32; h > 0; h >>= 1)  // pairwise, fixed order
+#pragma unroll
+          for (int q = 0; q < h; ++q) {
+            a[q].x += a[q + h].x;
+            a[q].y += a[q + h].y;
+          }
+        v = a[0];
       }
       for (int o = 8; o > 0; o >>= 1) {  // within each group of 16 lanes
         v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
@@ -545,7 +558,7 @@ bool launch_qr_blocked(double2* U, int d0, int d1, int d2, int leg, double tol, 
       cfg.attrs = at;
       cfg.numAttrs = 1;
       return cudaLaunchKernelEx(&cfg, k_qb_panel_grid, A, (int64_t)m, pn.c0, pn.nb, (const double*)sc, beta, alpha,
-                                phase, skip, pn.T, work + L.rec, work + L.own, work + L.gp, work + L.gf, bar + idx,
+                                phase, skip, pn.T, work + L.rec, work + L.own, work + L.gp, work + L.gf, bar + 8 * idx,
                                 flag) == cudaSuccess;
     }
     return launch_qr_panel(pn, s);
