@@ -252,19 +252,27 @@ __device__ __forceinline__ uint64_t gtimer() {
 // reaches target. The wait is bounded by the kernel-wide deadline; on expiry
 // bit 2 of *flag is set and false returned.
 constexpr int kBarLanes = 8;
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// The CTA barrier orders the CTA's earlier writes before thread 0's release;
+// the acquire of the counters plus the CTA barrier after it order the other
+// CTAs' writes before this CTA's later reads.
 __device__ bool grid_arrive_wait(unsigned* bar, unsigned target, bool wait, uint64_t deadline, int* flag) {
   __shared__ int s_ok;
-  __syncthreads();  // the CTA's writes before the barrier ...
+  __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
-    if (lane == 0) {
-      __threadfence();  // ... ordered before the arrival
-      atomicAdd(bar + blockIdx.x % kBarLanes, 1u);
-    }
+    if (lane == 0) red_release_add(bar + blockIdx.x % kBarLanes, 1u);
     int ok = 1;
     if (wait) {
       for (;;) {
-        unsigned v = lane < kBarLanes ? *(volatile unsigned*)(bar + lane) : 0u;
+        unsigned v = lane < kBarLanes ? ld_acquire(bar + lane) : 0u;
         for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (__shfl_sync(0xffffffffu, v, 0) >= target) break;
         if (__shfl_sync(0xffffffffu, (int)(gtimer() > deadline), 0)) {  // warp-uniform decision
@@ -273,7 +281,6 @@ __device__ bool grid_arrive_wait(unsigned* bar, unsigned target, bool wait, uint
           break;
         }
       }
-      __threadfence();
     }
     if (lane == 0) s_ok = ok;
   }
@@ -341,6 +348,8 @@ __global__ void __launch_bounds__(256) k_qb_panel_grid(double2* A, int64_t m, in
     if (alive) alive = grid_arrive_wait(bar, (unsigned)((j + 1) * G), true, deadline, flag);
     {  // sum the G records in a fixed order: 16 threads per task, then a butterfly
       const int task = tid >> 4, sub = tid & 15;
+      // the owner's record, loaded together with the CTA records
+      const double2 ow = tid < nb - j ? __ldcg(&own[j * kNB + j + tid]) : make_double2(0.0, 0.0);
       double2 v = make_double2(0.0, 0.0);
       if (task < nb - j) {
         double2 a[kBlkCap / 16];
@@ -363,7 +372,7 @@ __global__ void __launch_bounds__(256) k_qb_panel_grid(double2* A, int64_t m, in
         v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
       }
       if (sub == 0 && task < nb - j) red[task] = v;
-      if (tid < nb - j) s_own[tid] = __ldcg(&own[j * kNB + j + tid]);
+      if (tid < nb - j) s_own[tid] = ow;
     }
     __syncthreads();
     if (wid == 0) {  // alpha, phi, beta as in the cluster kernel (two lanes share a sqrt and a division)
