@@ -105,3 +105,40 @@ def test_rank64_tensor_cores_match_cuda_cores(pkg):
     gb.close()
     assert e_tc <= 1e-6 and e_ref <= 1e-6
     assert diff <= 1e-6
+
+
+def test_rank64_generic_state_node_tensors_4096x64_qr(pkg):
+    """A generic full-rank tree (random semi-unitary cores, random root) on the
+    4-site rank-64 chain: after one ps1 step every node tensor -- i.e. the Q
+    factors of the 4096 x 64 blocked QRs (panels over the whole GPU) and of the
+    cluster QRs, with their phase convention -- matches the oracle element by
+    element, not only the gauge-invariant rho_S."""
+    w = W.exciton_chain(n_sites=4, depth=4, rank=64)
+    o = ottn.from_workload(w)
+    assert any(T.shape == (64, 64, 64) for T in o.tensors)
+    rng = np.random.default_rng(64)
+    tensors = []
+    for u, T in enumerate(o.tensors):
+        X = rng.normal(size=T.shape) + 1j * rng.normal(size=T.shape)
+        if u == 0:
+            X /= np.linalg.norm(X)
+        else:  # semi-unitary toward the parent (leg 0)
+            M = np.moveaxis(X, 0, -1)
+            sh = M.shape
+            Q, _ = np.linalg.qr(M.reshape(-1, sh[-1]))
+            X = np.moveaxis(Q.reshape(sh), -1, 0)
+        tensors.append(X)
+    o.tensors = [t.copy() for t in tensors]
+    for c in o.tree.postorder():
+        if c:
+            o.update_env(c, o.tree.parent[c])
+    g = gpu_from(pkg, w)
+    for u, t in enumerate(tensors):
+        g.ttn_set_node(u, t)
+    g.ttn_step(w.dt, pkg.TTN_PS1, 1)
+    o.step(w.dt, "ps1")
+    errs = [float(np.max(np.abs(g.ttn_get_node(u) - o.tensors[u]))) for u in range(len(w.parent))]
+    rdm_err = float(np.max(np.abs(g.ttn_rdm() - o.rdm())))
+    g.close()
+    assert max(errs) < 1e-10, errs
+    assert rdm_err < 1e-10
