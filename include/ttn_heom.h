@@ -170,7 +170,11 @@ ttn_status ttn_set_rdo0(ttn_t h, const double* rho0);
  * generator on a non-default stream the kernels of one ps1 step are captured
  * once as a CUDA graph (per dt) and replayed. A non-finite amplitude is
  * detected on the device once per call and reported as TTN_ENUMERIC by the
- * next synchronising call (ttn_rdm, ttn_get_node). */
+ * next synchronising call (ttn_rdm, ttn_get_node). Kernels whose blocks wait on
+ * one another (the QR of a cluster of CTAs; the panels of the blocked QR of
+ * matricisations taller than a cluster holds, a cooperative launch of one
+ * CTA per SM) bound every wait to a few seconds; a wait that gives up is
+ * reported as TTN_ETIMEOUT by the next synchronising call. */
 ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps);
 
 /* rho_S = <0|Omega>: contract every feature leg with the n = 0 vector.

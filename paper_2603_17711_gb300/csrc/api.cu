@@ -1160,7 +1160,7 @@ static ttn_status check_flag(ttn_t h) {
   int flag = 0;
   CUDA_TRY(h, cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  if (flag & 2) return h->fail(TTN_ETIMEOUT, "a cluster exchange of the QR kernel gave up after 2 s");
+  if (flag & 2) return h->fail(TTN_ETIMEOUT, "a cluster or grid exchange of the QR kernels gave up after 2 s");
   if (flag & 8) return h->fail(TTN_ETIMEOUT, "a tensor-core MMA wait gave up after 1 s");
   if (flag) return h->fail(TTN_ENUMERIC, "non-finite amplitude in the root tensor");
   return TTN_OK;
