@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 TOL_SHORT = 1e-10
 TOL_FP64 = 1e-6
+TOL_MIXED = 1e-6  # the accuracy bar of the mixed form on rho_S (max-abs)
 
 
 @pytest.fixture(scope="module")
@@ -285,6 +286,27 @@ def test_batched_instances_equal_individual_runs(pkg):
         g.ttn_step(0.01, pkg.TTN_PS1, 2)
     for gb, ga in zip(batch, alone):
         assert np.array_equal(gb.ttn_rdm(), ga.ttn_rdm())
+    for g in batch + alone:
+        g.close()
+
+
+def test_batched_mixed_instances_equal_individual_runs(pkg):
+    """The mixed form (FP32 contractions, the largest nodes on the tensor
+    cores) under ttn_batch_step: bitwise the results of stepping each
+    instance alone in the same form, and within the mixed-form tolerance of
+    the FP64 oracle."""
+    ws = W.spin_boson_batch(n=6, n_steps=6)
+    batch = [gpu_from(pkg, w, precision=pkg.TTN_MIXED_FP32) for w in ws]
+    alone = [gpu_from(pkg, w, precision=pkg.TTN_MIXED_FP32) for w in ws]
+    pkg.ttn_batch_step(batch, 0.01, pkg.TTN_PS1, 6)
+    for g in alone:
+        g.ttn_step(0.01, pkg.TTN_PS1, 6)
+    for gb, ga, w in zip(batch, alone, ws):
+        assert np.array_equal(gb.ttn_rdm(), ga.ttn_rdm())
+        o = ottn.from_workload(w)
+        for _ in range(6):
+            o.step(0.01, "ps1")
+        assert np.max(np.abs(gb.ttn_rdm() - o.rdm())) <= TOL_MIXED
     for g in batch + alone:
         g.close()
 
