@@ -306,6 +306,26 @@ def bench_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         ms_b = ta.elapsed_time(tb)
         k1 = sum(hh.ttn_stats(0)[1] for hh in hs) / (args.warmup + args.steps)
+        rho_b = [hh.ttn_rdm() for hh in hs]
+        # the same instances in the mixed form (FP32 contractions, tensor cores
+        # for nodes >= 16384 elements), same steps, against the FP64 batch
+        hm = [make_gpu(pkg, bw, local_rank, precision=pkg.TTN_MIXED_FP32) for bw in bws]
+        for hh in hm:
+            hh.ttn_set_params(max_split=1)
+        pkg.ttn_batch_step(hm, 0.01, 1, args.warmup)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(hm[0].stream):
+            flush.zero_()
+        ta.record(hm[0].stream)
+        pkg.ttn_batch_step(hm, 0.01, 1, args.steps)
+        tb.record(hm[0].stream)
+        torch.cuda.synchronize()
+        ms_bm = ta.elapsed_time(tb)
+        errs = [float(np.max(np.abs(hh.ttn_rdm() - rb))) for hh, rb in zip(hm, rho_b)]
+        scale = [float(np.max(np.abs(rb))) for rb in rho_b]
+        bounded = [e for e, sc in zip(errs, scale) if sc <= 1.0 + 1e-9]  # |rho_ij| <= 1 (physical range)
+        for hh in hm:
+            hh.close()
         # the same instances one after another (each its own step graph), few steps
         n_seq = 2
         torch.cuda.synchronize()
@@ -322,6 +342,13 @@ def bench_ours(args, rank, world, local_rank):
                      "ms_per_batched_step": ms_b / args.steps,
                      "sequential_instance_steps_per_s": args.batch * n_seq / seq_s,
                      "node_contraction_gflop_per_batched_step": k1 / 1e9,
+                     "mixed_fp32": {"instance_steps_per_s": args.batch * args.steps / (ms_bm * 1e-3),
+                                    "ms_per_batched_step": ms_bm / args.steps,
+                                    "rdm_max_abs_vs_fp64_batch": max(errs),
+                                    "rdm_max_rel_vs_fp64_batch": max(e / max(1.0, sc) for e, sc in zip(errs, scale)),
+                                    "rdm_max_abs_vs_fp64_batch_physical": max(bounded) if bounded else None,
+                                    "instances_outside_physical_range": len(errs) - len(bounded),
+                                    "steps_compared": args.warmup + args.steps},
                      "l2": "one 256 MB flush before the timed batch (the 256 states total ~0.3 GB)"}
 
     # ---- end to end through the public API with host buffers ----
