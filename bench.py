@@ -142,6 +142,22 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # GPU leg
 # ----------------------------------------------------------------------------
+def replica_max(x: float, dist, device) -> float:
+    """The largest per-rank value over the ranks (the slowest replica's time);
+    x itself when there is no process group."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(world: int, steps: int, ms_max: float) -> float:
+    """Whole-job steps/s of `world` replicas that each ran `steps` steps, timed
+    by the slowest one."""
+    return world * steps / (ms_max * 1e-3)
+
+
 def make_gpu(pkg, w, device, precision=0):
     return pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0,
                           drives=w.drives, device=device, precision=precision)
@@ -242,10 +258,7 @@ def bench_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     launches = sum(g.ttn_stats(k)[0] for k in range(4))
     flops = {k: g.ttn_stats(k)[1] for k in range(4)}
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = replica_max(ms, dist, dev)
 
     # ---- per-kernel-class device time (roofline of the dominant kernel) ----
     g.ttn_stats_reset()
@@ -363,10 +376,7 @@ def bench_ours(args, rank, world, local_rank):
     sop = pkg.heom.heom_sop(w.H, w.baths, w.depth, w.drives)
     h2d = sum(np.asarray(v).nbytes for v in sop.values()) + w.rho0.nbytes
     g2.close()
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_s = float(e2e_t.item())
+    e2e_s = replica_max(e2e_s, dist, dev)
 
     if rank != 0:
         return
@@ -375,7 +385,7 @@ def bench_ours(args, rank, world, local_rank):
     n_l, fl, t_ms = prof[dom]
     achieved = fl / (t_ms * 1e-3) / 1e12 if t_ms > 0 else 0.0
     k1_launches, k1_flops, k1_ms = prof[0]
-    value = world * args.steps / (ms_max * 1e-3)
+    value = replicas_value(world, args.steps, ms_max)
     out = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
