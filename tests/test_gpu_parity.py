@@ -406,3 +406,62 @@ def test_autotuned_handle_matches_oracle(pkg):
             err = max(err, float(np.max(np.abs(g.ttn_rdm() - o.rdm()))))
         g.close()
         assert err <= tol, (prec, err)
+
+
+# ---------------------------------------------------------------------------
+# Bonds wider than 64 (ranks up to 256 are accepted): the QR matricisations
+# 81 x 81 and 324 x 81 exceed the cluster and blocked kernels' 64 columns and
+# run on the one-CTA Householder kernel.
+# ---------------------------------------------------------------------------
+def _wide_bond_workload():
+    w = W.spin_boson_tt(depth=9, n_pade=3, rank=96, tree="btt")
+    o = ottn.from_workload(w)
+    assert max(o.ranks) == 81
+    return w, o
+
+
+def test_bonds_wider_than_64_product_state(pkg):
+    w, _ = _wide_bond_workload()
+    err, g, _ = run_both(pkg, w, 10)
+    assert max(g.ttn_get_ranks()) == 81
+    g.close()
+    assert err <= TOL_SHORT
+
+
+def test_bonds_wider_than_64_generic_state_node_tensors(pkg):
+    """From a generic full-rank tree every node tensor after two steps -- the Q
+    factors of the 81-column QRs with their phase convention -- matches the
+    oracle, in FP64 (1e-10) and, for rho_S, in the mixed form (1e-6)."""
+    w, o = _wide_bond_workload()
+    rng = np.random.default_rng(81)
+    tensors = []
+    for u, T in enumerate(o.tensors):
+        X = rng.normal(size=T.shape) + 1j * rng.normal(size=T.shape)
+        if u == 0:
+            X /= np.linalg.norm(X)
+        else:
+            M = np.moveaxis(X, 0, -1)
+            sh = M.shape
+            Q, _ = np.linalg.qr(M.reshape(-1, sh[-1]))
+            X = np.moveaxis(Q.reshape(sh), -1, 0)
+        tensors.append(X)
+    o.tensors = [t.copy() for t in tensors]
+    for c in o.tree.postorder():
+        if c:
+            o.update_env(c, o.tree.parent[c])
+    ga = gpu_from(pkg, w)
+    gb = gpu_from(pkg, w, precision=pkg.TTN_MIXED_FP32)
+    for g in (ga, gb):
+        for u, t in enumerate(tensors):
+            g.ttn_set_node(u, t)
+        g.ttn_step(w.dt, pkg.TTN_PS1, 2)
+    for _ in range(2):
+        o.step(w.dt, "ps1")
+    errs = [float(np.max(np.abs(ga.ttn_get_node(u) - o.tensors[u]))) for u in range(len(w.parent))]
+    e_fp64 = float(np.max(np.abs(ga.ttn_rdm() - o.rdm())))
+    e_mixed = float(np.max(np.abs(gb.ttn_rdm() - o.rdm())))
+    ga.close()
+    gb.close()
+    assert max(errs) < 1e-10, errs
+    assert e_fp64 <= TOL_SHORT
+    assert e_mixed <= TOL_MIXED
