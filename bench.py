@@ -218,6 +218,42 @@ def rank64_leg(args, pkg, torch, flush, local_rank, forms=(("fp64", 0), ("mixed_
     return out
 
 
+def accuracy_leg(args, pkg, torch, w, local_rank):
+    """rho_S of the mixed form against the FP64 form over a long trajectory of
+    the bench workload: max-abs difference over all steps, at the end, and the
+    trace drift of each form."""
+    ga = make_gpu(pkg, w, local_rank)
+    if args.accuracy_vs == "mixed":
+        gb = make_gpu(pkg, w, local_rank, precision=pkg.TTN_MIXED_FP32)
+    else:  # FP64 again, with another summation order (no CTA split of the contractions)
+        gb = make_gpu(pkg, w, local_rank)
+        gb.ttn_set_params(max_split=1)
+    t0 = np.trace(ga.ttn_rdm()).real
+    worst, worst_step = 0.0, 0
+    trail = []  # (step, max-abs difference) at about 20 points along the run
+    every_trail = max(1, args.accuracy_steps // 20)
+    for k in range(args.accuracy_steps):
+        ga.ttn_step(w.dt, 1, 1)
+        gb.ttn_step(w.dt, 1, 1)
+        if (k + 1) % args.accuracy_every == 0 or k + 1 == args.accuracy_steps:
+            ra, rb = ga.ttn_rdm(), gb.ttn_rdm()
+            e = float(np.max(np.abs(ra - rb)))
+            if e > worst:
+                worst, worst_step = e, k + 1
+            if (k + 1) % every_trail == 0:
+                trail.append([k + 1, e, float(np.max(np.abs(ra)))])
+    out = {"workload": WORKLOAD, "steps": args.accuracy_steps, "compared_every": args.accuracy_every,
+           "compared": "FP64 vs " + ("mixed FP32" if args.accuracy_vs == "mixed" else "FP64 with another summation order"),
+           "rdm_max_abs_mixed_vs_fp64": worst, "at_step": worst_step,
+           "rdm_max_abs_at_end": float(np.max(np.abs(ra - rb))),
+           "trace_drift_fp64": float(abs(np.trace(ra).real - t0)),
+           "trace_drift_mixed": float(abs(np.trace(rb).real - t0)),
+           "trail_step_err_maxabsrho": trail}
+    ga.close()
+    gb.close()
+    return out
+
+
 def bench_ours(args, rank, world, local_rank):
     import torch
     import paper_2603_17711_gb300 as pkg
@@ -228,6 +264,10 @@ def bench_ours(args, rank, world, local_rank):
         import torch.distributed as dist
     w = workload()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    if args.accuracy_steps:  # long trajectory: mixed against FP64 on the GPU, step by step
+        if rank == 0:
+            print(json.dumps({"accuracy": accuracy_leg(args, pkg, torch, w, local_rank)}), flush=True)
+        return
     if args.rank64_only:  # profiling aid: only the rank-64 leg, in the form asked for
         forms = (("fp64", 0),) if args.rank64_only == "fp64" else (("mixed_fp32", pkg.TTN_MIXED_FP32),)
         if rank == 0:
@@ -474,6 +514,11 @@ def main():
     ap.add_argument("--rank64-only", choices=["fp64", "mixed"], default=None,
                     help="profiling aid: run only the rank-64 leg in one form (prints that object, not the bench line)")
     ap.add_argument("--batch", type=int, default=256, help="instances in the batched leg")
+    ap.add_argument("--accuracy-steps", type=int, default=0,
+                    help="run only a long mixed-vs-FP64 trajectory of this many steps (prints that object)")
+    ap.add_argument("--accuracy-every", type=int, default=10, help="compare rho_S every this many steps")
+    ap.add_argument("--accuracy-vs", choices=["mixed", "fp64-order"], default="mixed",
+                    help="second run of the accuracy trajectory: the mixed form, or FP64 with other launch shapes")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
