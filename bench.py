@@ -244,10 +244,10 @@ def accuracy_leg(args, pkg, torch, w, local_rank):
                 trail.append([k + 1, e, float(np.max(np.abs(ra)))])
     out = {"workload": WORKLOAD, "steps": args.accuracy_steps, "compared_every": args.accuracy_every,
            "compared": "FP64 vs " + ("mixed FP32" if args.accuracy_vs == "mixed" else "FP64 with another summation order"),
-           "rdm_max_abs_mixed_vs_fp64": worst, "at_step": worst_step,
+           "rdm_max_abs_diff": worst, "at_step": worst_step,
            "rdm_max_abs_at_end": float(np.max(np.abs(ra - rb))),
            "trace_drift_fp64": float(abs(np.trace(ra).real - t0)),
-           "trace_drift_mixed": float(abs(np.trace(rb).real - t0)),
+           "trace_drift_second": float(abs(np.trace(rb).real - t0)),
            "trail_step_err_maxabsrho": trail}
     ga.close()
     gb.close()
