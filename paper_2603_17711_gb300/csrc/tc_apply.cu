@@ -104,10 +104,28 @@ __device__ __forceinline__ Geo3 geo_of(const ApOut& o) {
 // 32 K columns covers 16 leg indices x; each complex value is read once.
 // base[nn]: offset of tile position nn over the two other legs.
 constexpr int kAq = (kTcM / 2) * (kTcK / 2) / kTcThreads;  // complex operator entries per thread and chunk
-constexpr int kBq = kTcN * (kTcK / 2) / kTcThreads;        // complex tensor entries per thread and chunk
+// The tensor operand is staged in items of one tile position nn and a pair
+// of leg indices (2 xp, 2 xp + 1): their four floats (re, im, re, im) are one
+// 16-byte row of a core matrix, written with one vector store per hi / lo
+// plane; eight consecutive positions fill 128 contiguous bytes, so a warp's
+// store touches each bank once per 128 bytes.
+constexpr int kBp = kTcN * (kTcK / 4) / kTcThreads;  // (position, leg pair) items per thread and chunk
+static_assert(kTcK / 4 == 8 && kTcN % 8 == 0, "item mapping below");
 struct ChunkRegs {
-  float2 m[kAq], x[kBq];
+  float2 m[kAq], x[2 * kBp];
 };
+// item e -> (nn, xp). Leg contiguous in X (x_fast): eight consecutive items
+// are eight positions (one 128-byte smem segment), the next bits the pair;
+// otherwise consecutive items are consecutive positions (contiguous in X).
+__device__ __forceinline__ void b_item(int e, bool x_fast, int& nn, int& xp) {
+  if (x_fast) {
+    nn = ((e >> 6) << 3) | (e & 7);
+    xp = (e >> 3) & 7;
+  } else {
+    nn = e % kTcN;
+    xp = e / kTcN;
+  }
+}
 
 // Load this thread's share of chunk kc (one L2 round trip; the values are
 // split and stored later, so the loads overlap the MMAs of the previous chunk).
@@ -121,11 +139,13 @@ __device__ __forceinline__ void load_chunk(ChunkRegs& r, const float2* __restric
     r.m[q] = (i < d && x < d) ? M[i * d + x] : make_float2(0.f, 0.f);
   }
 #pragma unroll
-  for (int q = 0; q < kBq; ++q) {
-    // consecutive threads walk the contiguous direction of X
-    const int e = threadIdx.x + q * kTcThreads;
-    const int nn = x_fast ? e >> 4 : e % kTcN, x = x0 + (x_fast ? e & 15 : e / kTcN);
-    r.x[q] = (nn < nvalid && x < d) ? X[(int64_t)x * st_l + base[nn]] : make_float2(0.f, 0.f);
+  for (int q = 0; q < kBp; ++q) {
+    int nn, xp;
+    b_item(threadIdx.x + q * kTcThreads, x_fast, nn, xp);
+    const int x = x0 + 2 * xp;
+    const bool ok = nn < nvalid;
+    r.x[2 * q] = (ok && x < d) ? X[(int64_t)x * st_l + base[nn]] : make_float2(0.f, 0.f);
+    r.x[2 * q + 1] = (ok && x + 1 < d) ? X[(int64_t)(x + 1) * st_l + base[nn]] : make_float2(0.f, 0.f);
   }
 }
 // Split into tf32 hi / lo, embed, and store into one stage buffer.
@@ -148,15 +168,15 @@ __device__ __forceinline__ void store_chunk(float* buf, const ChunkRegs& r, bool
     }
   }
 #pragma unroll
-  for (int q = 0; q < kBq && with_b; ++q) {
-    const int e = threadIdx.x + q * kTcThreads;
-    const int nn = x_fast ? e >> 4 : e % kTcN, xl = x_fast ? e & 15 : e / kTcN;
-    const int o0 = cm_off(nn, 2 * xl), o1 = cm_off(nn, 2 * xl + 1);
-    const float h0 = tf32_hi(r.x[q].x), h1 = tf32_hi(r.x[q].y);
-    Bh[o0] = h0;
-    Bl[o0] = tf32_hi(r.x[q].x - h0);
-    Bh[o1] = h1;
-    Bl[o1] = tf32_hi(r.x[q].y - h1);
+  for (int q = 0; q < kBp && with_b; ++q) {
+    int nn, xp;
+    b_item(threadIdx.x + q * kTcThreads, x_fast, nn, xp);
+    const int o = cm_off(nn, 4 * xp);  // K positions 4 xp .. 4 xp + 3: one 16-byte row
+    const float2 a = r.x[2 * q], b = r.x[2 * q + 1];
+    const float4 h = make_float4(tf32_hi(a.x), tf32_hi(a.y), tf32_hi(b.x), tf32_hi(b.y));
+    *reinterpret_cast<float4*>(Bh + o) = h;
+    *reinterpret_cast<float4*>(Bl + o) =
+        make_float4(tf32_hi(a.x - h.x), tf32_hi(a.y - h.y), tf32_hi(b.x - h.z), tf32_hi(b.y - h.w));
   }
 }
 
