@@ -396,28 +396,29 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
   int64_t poffs[2] = {-1, -1};
   int kcs[2] = {0, 0};
   ChunkRegs R0, R1;
-  auto fetch = [&](int ci, ChunkRegs& R) {
+  const int64_t st_l = g.st[leg];  // stride of the contracted leg, read once
+  // slot = ci & 1, passed as a literal so that these small arrays stay in registers
+  auto fetch = [&](int ci, ChunkRegs& R, int slot) {
     const float2 *M, *X;
     int kc;
     int64_t poff;
     chunk_src(ci, M, X, kc, poff);
-    bulk[ci & 1] = poff >= 0;
-    poffs[ci & 1] = poff;
-    kcs[ci & 1] = kc;
-    load_chunk(R, M, X, d, g.st[leg], leg == 2, base, nvalid, kc, !bulk[ci & 1]);
+    bulk[slot] = poff >= 0;
+    poffs[slot] = poff;
+    kcs[slot] = kc;
+    load_chunk(R, M, X, d, st_l, leg == 2, base, nvalid, kc, !bulk[slot]);
   };
-  fetch(0, R0);
+  fetch(0, R0, 0);
   if (bulk[0]) bulk_a(tsm, poffs[0], kcs[0], 0);
   store_chunk(tsm, R0, leg == 2, !bulk[0]);
-  if (nchunks > 1) fetch(1, R1);
+  if (nchunks > 1) fetch(1, R1, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
   // one iteration: MMAs of chunk ci; loads of chunk ci+2 into Rld; chunk ci+1
   // (in Rst since the previous iteration) stored into the other stage
-  auto step = [&](int ci, ChunkRegs& Rst, ChunkRegs& Rld) {
-    const int b = ci & 1;
+  auto step = [&](int ci, ChunkRegs& Rst, ChunkRegs& Rld, int b) {  // b = ci & 1, a literal
     float* buf = tsm + b * kStageFloats;
     // make the staged operands visible to the tensor core, then issue
     if (bulk[b] && ok) {
@@ -431,7 +432,9 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
     if (tid == 0 && ok) {
       const uint32_t ah = smem_u32(buf), al = ah + kAElems * 4, bh = al + kAElems * 4, bl = bh + kBElems * 4;
       const uint32_t a_op[3] = {ah, ah, al}, b_op[3] = {bh, bl, bh};
+#pragma unroll
       for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
         for (int ks = 0; ks < kTcK / 8; ++ks) {
           const uint64_t ad = sdesc(a_op[pass] + ks * 256), bd = sdesc(b_op[pass] + ks * 256);
           const uint32_t accum = (ci > 0 || pass > 0 || ks > 0) ? 1u : 0u;
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
                        smem_u32(&mbar[b]))
                    : "memory");
     }
-    if (ci + 2 < nchunks) fetch(ci + 2, Rld);
+    if (ci + 2 < nchunks) fetch(ci + 2, Rld, b);
     if (ci + 1 < nchunks) {
       // the other stage is free once the MMAs of chunk ci-1 have completed
       if (ci >= 1 && ok) {
@@ -457,11 +460,14 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
     }
   };
   for (int ci = 0; ci < nchunks; ci += 2) {
-    step(ci, R1, R0);
-    if (ci + 1 < nchunks) step(ci + 1, R0, R1);
+    step(ci, R1, R0, 0);
+    if (ci + 1 < nchunks) step(ci + 1, R0, R1, 1);
   }
   // all MMAs done once the last commit has landed (they complete in order)
-  if (ok) ok = mbar_wait(&mbar[(nchunks - 1) & 1], ph[(nchunks - 1) & 1], deadline);
+  if (ok) {
+    const bool odd = ((nchunks - 1) & 1) != 0;
+    ok = mbar_wait(odd ? &mbar[1] : &mbar[0], odd ? ph[1] : ph[0], deadline);
+  }
   ok = __syncthreads_and(ok) != 0;  // CTA-uniform: tcgen05.ld below is warp-collective
   if (!ok && tid == 0) atomicOr(flag, 8);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
