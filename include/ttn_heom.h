@@ -75,9 +75,12 @@ typedef struct {
 } ttn_tree;
 
 /* Numerical parameters (defaults in parentheses).
- *  qr_tol    (1e-12) Householder QR treats a column whose remaining norm is at
+ *  qr_tol    (1e-9)  Householder QR treats a column whose remaining norm is at
  *                    most qr_tol*||A||_F as exactly dependent: no reflector,
- *                    R_jj = 0, Q column = H_0..H_{j-1} e_j.
+ *                    R_jj = 0, Q column = H_0..H_{j-1} e_j. Much smaller
+ *                    values let rounding decide the completion of nearly
+ *                    dependent columns, and long fixed-rank trajectories then
+ *                    depend on the order of the sums.
  *  kappa     (2.5)   RK4 substeps per flow of length tau:
  *                    m = max(1, ceil(|tau| * Lambda / kappa - 1e-9)), Lambda =
  *                    sum over terms of |coef| * prod ||op||_2 (|coef| * g_bound

@@ -263,7 +263,7 @@ def _complete_columns(Qg: np.ndarray, r: int) -> np.ndarray:
 
 @dataclasses.dataclass
 class Params:
-    qr_tol: float = 1e-12
+    qr_tol: float = 1e-9
     kappa: float = 2.5
     ps2_atol: float = 1e-7
     ps2_ratio: float = 2.0

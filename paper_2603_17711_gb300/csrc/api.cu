@@ -32,7 +32,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct ttn_ctx {
   Plan plan;
   int precision = TTN_FP64;
-  ttn_params params{1e-12, 2.5, 1e-7, 2.0, 32, 1e-12, kMaxSplit, 1};
+  ttn_params params{1e-9, 2.5, 1e-7, 2.0, 32, 1e-12, kMaxSplit, 1};
   bool sop_loaded = false;
   bool ws_bound = false;
   bool envs_dirty = true;

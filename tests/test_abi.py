@@ -86,7 +86,7 @@ def test_params_round_trip_and_range_checks(lib):
     assert st == 0
     p = _lib.ttn_params()
     assert lib.ttn_get_params(h, C.byref(p)) == 0
-    assert (p.qr_tol, p.kappa, p.max_rank, p.max_split, p.tensor_cores) == (1e-12, 2.5, 32, 8, 1)
+    assert (p.qr_tol, p.kappa, p.max_rank, p.max_split, p.tensor_cores) == (1e-9, 2.5, 32, 8, 1)
     for field, bad in (("max_split", 0), ("max_split", 9), ("kappa", 0.0), ("ps2_ratio", 0.5), ("max_rank", 0),
                        ("tensor_cores", 2)):
         q = _lib.ttn_params()
