@@ -465,3 +465,29 @@ def test_bonds_wider_than_64_generic_state_node_tensors(pkg):
     assert max(errs) < 1e-10, errs
     assert e_fp64 <= TOL_SHORT
     assert e_mixed <= TOL_MIXED
+
+
+# ---------------------------------------------------------------------------
+# Long fixed-rank trajectories: with the QR dependence threshold at 1e-9 the
+# completion of nearly dependent columns no longer depends on rounding, so
+# runs that differ only in the order of their sums, or in the precision of
+# the contractions, stay together over the whole trajectory.
+# ---------------------------------------------------------------------------
+def test_long_trajectory_reproducible_and_mixed_within_bar(pkg):
+    w = W.exciton_chain(rank=20)
+    ga = gpu_from(pkg, w)
+    gb = gpu_from(pkg, w)
+    gb.ttn_set_params(max_split=1)  # another summation order of every split contraction
+    gc = gpu_from(pkg, w, precision=pkg.TTN_MIXED_FP32)
+    e_order = e_mixed = 0.0
+    for k in range(1000):
+        for g in (ga, gb, gc):
+            g.ttn_step(w.dt, pkg.TTN_PS1, 1)
+        if (k + 1) % 50 == 0:
+            ra = ga.ttn_rdm()
+            e_order = max(e_order, float(np.max(np.abs(gb.ttn_rdm() - ra))))
+            e_mixed = max(e_mixed, float(np.max(np.abs(gc.ttn_rdm() - ra))))
+    for g in (ga, gb, gc):
+        g.close()
+    assert e_order <= 1e-10, e_order  # 8e-6 with the former 1e-12 threshold
+    assert e_mixed <= TOL_MIXED, e_mixed
