@@ -42,6 +42,28 @@ def test_householder_qr_rank_deficient_is_deterministic():
     assert np.max(np.abs(Q1 - Q2)) < 1e-9
 
 
+def test_default_qr_threshold_completes_nearly_dependent_columns_deterministically():
+    """A column that is dependent up to a 1e-11 relative remainder (what a
+    truncated state's padding directions look like after some steps): with the
+    default threshold it has no reflector and its Q column is the completion,
+    unchanged by 1e-16 noise; a threshold far below the remainder builds a
+    reflector from it instead (so rounding-sized noise in the remainder moves
+    that Q column at first order)."""
+    rng = np.random.default_rng(11)
+    B = _rand(rng, 40, 3)
+    near = B[:, :1] - 0.5 * B[:, 2:] + 1e-11 * np.linalg.norm(B) * _rand(rng, 40, 1)
+    A = np.concatenate([B, near], axis=1)
+    tol = ttn.Params().qr_tol
+    assert tol >= 1e-10
+    Q1, R1 = ttn.householder_qr(A, tol)
+    Q2, R2 = ttn.householder_qr(A + 1e-16 * _rand(rng, 40, 4), tol)
+    assert R1[3, 3] == 0.0 and R2[3, 3] == 0.0
+    assert np.max(np.abs(Q1 - Q2)) < 1e-12
+    assert np.max(np.abs(Q1.conj().T @ Q1 - np.eye(4))) < 1e-13
+    Qs, Rs = ttn.householder_qr(A, 1e-14)
+    assert abs(Rs[3, 3]) > 0.0  # a reflector built from the 1e-11 remainder
+
+
 def test_rk4_is_fourth_order():
     rng = np.random.default_rng(2)
     A = 0.5 * _rand(rng, 6, 6)
