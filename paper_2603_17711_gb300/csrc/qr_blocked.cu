@@ -2,9 +2,11 @@
 // shared memory (e.g. 4096 x 64 at bond rank 64), FP64.
 //
 // Same convention and, in exact arithmetic, the same result as the unblocked
-// kernels: the column loop is the cluster kernel run on panels of kQrPanelMaxNb
-// columns (rows from the panel's first pivot down), with the threshold
-// tol*||A||_F of the WHOLE matrix; the panel's reflectors are then applied to
+// kernels: the column loop runs on panels of kQrPanelMaxNb columns (rows from
+// the panel's first pivot down) with the threshold tol*||A||_F of the WHOLE
+// matrix -- over the whole GPU (k_qb_panel_grid, a cooperative launch with one
+// grid exchange per column) where the device supports cooperative launches,
+// else as the cluster kernel in panel mode; the panel's reflectors are then applied to
 // the trailing columns in compact WY form, A2 -= V T^H (V^H A2), and Q is formed
 // by applying the panels in reverse order to the first n columns of the
 // identity, X -= V T (V^H X). A skipped column has no reflector (zero v, zero
@@ -14,8 +16,7 @@
 //
 // The trailing and Q updates are spread over one CTA per SM (rows split evenly,
 // at most kRB per CTA): they are bound by the FP64 issue rate of each SM, so
-// an even split over all SMs is what shortens them. Only the panels run on
-// one cluster.
+// an even split over all SMs is what shortens them.
 #include <algorithm>
 
 #include "kernels.cuh"
