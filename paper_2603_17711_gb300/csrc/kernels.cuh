@@ -92,7 +92,9 @@ bool launch_project_tiled(int prec, const DevTables& T, const PjList& L, int d, 
 // work: >= P complex, qbuf: >= P complex. A non-finite ||U||_F sets *flag and
 // leaves U unchanged. U_lo / R_lo (nullable) receive FP32 copies of Q and R.
 // work_elems: capacity of work (the blocked path for tall matrices needs
-// qr_blocked_elems(m, n) of it; otherwise P suffices).
+// qr_blocked_elems(m, n) of it; otherwise P suffices). Tried in order: the
+// cluster kernel (n <= 64, rows fit a cluster), the blocked path (n <= 64),
+// the one-CTA kernel (any n).
 void launch_qr(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work, int64_t work_elems,
                double2* qbuf, double2* R, int* flag, float2* U_lo, float2* R_lo, cudaStream_t s);
 // Cluster-parallel variant (qr.cu); returns false when the shape does not fit
@@ -122,7 +124,9 @@ constexpr int kQrPanelMaxNb = 16;
 bool launch_qr_panel(const QrPanel& pn, cudaStream_t s);
 int qr_panel_cluster(int m_act, int nb);  // cluster size of a panel, 0 if it does not fit
 // Blocked Householder QR for matrices the cluster kernel cannot hold; same
-// convention and result as launch_qr. work needs qr_blocked_elems(m, n)
+// convention and result as launch_qr. Panels run over the whole GPU (a
+// cooperative launch, bounded waits -> bit 2 of *flag) where the device
+// supports it, else on one cluster. work needs qr_blocked_elems(m, n)
 // complex values; returns false (nothing launched) when it does not apply.
 int64_t qr_blocked_elems(int64_t m, int64_t n);
 bool launch_qr_blocked(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work,
