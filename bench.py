@@ -12,6 +12,17 @@ Prints one JSON line (rank 0). Multi-GPU runs are independent replicas of the
 same propagation (a single TTN sweep has no data-parallel split), launched one
 process per GPU by torch.distributed.run; value = all steps of all ranks / the
 slowest rank's time.
+
+Beside the headline the line carries:
+- the mixed form (FP32 contractions) of the same workload;
+- the same chain at bond rank 64 in both forms;
+- 256 uneven spin-boson instances batched, in both forms;
+- the end-to-end rate through the API;
+- the roofline of the dominant kernel class;
+- the FP64 CPU oracle as cpu_baseline.
+
+--rank64-only and --accuracy-steps print only the rank-64 leg or a long rho_S
+trajectory comparison instead.
 """
 from __future__ import annotations
 
