@@ -99,7 +99,11 @@ typedef struct {
  *  tensor_cores (1)  mixed form only: run the mode products of large nodes
  *                    (contracted legs <= 64, >= 16384 elements) on the
  *                    tcgen05 tensor cores in 3xTF32 (hi/lo split, FP32
- *                    accumulation); 0 keeps them on the FP32 CUDA cores. */
+ *                    accumulation); 0 keeps them on the FP32 CUDA cores.
+ *  wait_s    (2.0)   0..60: upper bound, in seconds, of every device-side wait
+ *                    of the kernels whose blocks wait on one another (the grid
+ *                    barriers of the Jacobi SVD); a wait that runs out is
+ *                    reported as TTN_ETIMEOUT (no counterpart in the paper). */
 typedef struct {
   double qr_tol;
   double kappa;
@@ -109,6 +113,7 @@ typedef struct {
   double svd_tol;
   int32_t max_split;
   int32_t tensor_cores;
+  double wait_s;
 } ttn_params;
 
 /* Create a handle (Sec. 2.3, Eq. omega_tensor). leg_dims[n_legs]: leg
@@ -218,8 +223,13 @@ ttn_status ttn_batch_step(ttn_t* hs, int32_t n, double dt, int32_t scheme, int32
  * ttn_stats: launches and algorithmic FLOPs issued since the last reset
  * (complex multiply-add = 8 FLOPs), counted on the host, always on.
  * ttn_profile(h, 1) additionally brackets every launch with CUDA events on the
- * handle's stream; ttn_profile_read synchronises and returns the summed device
- * time of each class in milliseconds. ttn_stats_reset clears both. */
+ * handle's stream (the step is then issued launch by launch, not as a graph);
+ * ttn_profile(h, 2) keeps the captured step graph and records the bracketing
+ * events as event-record nodes inside it, so the times are those of the
+ * graph-replayed step (ttn_step then synchronises after every replay to read
+ * them; launches outside a graph are bracketed as in mode 1). 0 turns it off.
+ * ttn_profile_read synchronises and returns the summed device time of each
+ * class in milliseconds. ttn_stats_reset clears both. */
 ttn_status ttn_stats(ttn_t h, int32_t kind, int64_t* launches, double* flops);
 ttn_status ttn_profile(ttn_t h, int32_t on);
 ttn_status ttn_profile_read(ttn_t h, int32_t kind, double* ms);
@@ -276,7 +286,9 @@ ttn_status ttn_proposer_stats(ttn_t h, int64_t* proposed, int64_t* accepted);
  * node_dev[u] points to node u's tensor in canonical layout (the layout
  * ttn_get_node returns); tree, leg_dims and ranks are as for ttn_create. The
  * first call on each device looks up the array's device address with that
- * device current; make that first call before any CUDA stream capture. All
+ * device current; make that first call before any CUDA stream capture. The
+ * address is kept for the life of the process, so do not call this again on a
+ * device after cudaDeviceReset. Devices beyond ordinal 63 get TTN_EINVAL. All
  * calls on one device share the array, which keeps the last call's contents;
  * every entry a call reads it has written first, so nothing needs clearing.
  * Calls that overlap on the GPU (different streams or host threads) race on
@@ -298,6 +310,25 @@ ttn_status ttn_rdm_noalloc(const ttn_tree* tree, const int32_t* leg_dims, const 
  * change rebuilding a list, returns those lists to the built-in rule.
  * reps: 1..100. Errors: TTN_ESTATE before ttn_set_workspace, TTN_EINVAL. */
 ttn_status ttn_autotune(ttn_t h, int32_t reps);
+
+/* Singular value decomposition a = U diag(sigma) V^H of a device matrix by
+ * one-sided (Hestenes) Jacobi rotations in FP64: the factorisation the ps2
+ * scheme uses to split a merged pair (Sec. 2.3, last paragraph), exposed for
+ * callers and tests. a_dev: m x n complex, row-major (not modified); k =
+ * min(m, n). Outputs: u_dev m x k and vh_dev k x n (device, row-major), sigma_host
+ * k values in descending order; singular vectors of sigma = 0 are returned as
+ * zero. ws_dev: ttn_svd_workspace_size(m, n) bytes, 256-byte aligned. Matrices
+ * whose smaller side has 24 or more columns run over the whole GPU (the pairs
+ * of each round of the circle ordering spread over the CTAs of one cooperative
+ * launch, one grid barrier per round); every barrier wait is bounded by
+ * wait_s seconds (0..60). *sweeps_out (nullable): sweeps that rotated.
+ * Synchronises `stream` (cudaStream_t as void*). Errors: TTN_EINVAL,
+ * TTN_ENOMEM (workspace too small or misaligned), TTN_ETIMEOUT (a barrier
+ * wait gave up; outputs undefined), TTN_ENUMERIC (no convergence within 60
+ * sweeps), TTN_ECUDA. */
+ttn_status ttn_svd_workspace_size(int32_t m, int32_t n, size_t* bytes);
+ttn_status ttn_svd(const void* a_dev, int32_t m, int32_t n, void* u_dev, double* sigma_host, void* vh_dev,
+                   void* ws_dev, size_t ws_bytes, double wait_s, int32_t* sweeps_out, void* stream);
 
 const char* ttn_last_error(ttn_t h);
 void ttn_destroy(ttn_t h);

@@ -171,8 +171,11 @@ class TTN:
         self._check(self.lib.ttn_stats(self.h, kind, C.byref(n), C.byref(f)), "ttn_stats")
         return int(n.value), float(f.value)
 
-    def ttn_profile(self, on: bool) -> None:
-        self._check(self.lib.ttn_profile(self.h, 1 if on else 0), "ttn_profile")
+    def ttn_profile(self, on) -> None:
+        """on: False/0 off, True/1 events around every launch (no step graph),
+        2 events as nodes inside the replayed step graph."""
+        mode = 2 if on == 2 else (1 if on else 0)
+        self._check(self.lib.ttn_profile(self.h, mode), "ttn_profile")
 
     def ttn_profile_read(self, kind: int) -> float:
         ms = C.c_double()
@@ -326,3 +329,31 @@ def from_model(H, baths, depth, parent, leg_node, ranks, rho0=None, drives=(), p
     if rho0 is not None:
         t.ttn_set_rdo0(rho0)
     return t
+
+
+def svd(a, wait_s: float = 2.0):
+    """FP64 Jacobi SVD of a complex128 CUDA matrix through the C ABI ttn_svd:
+    returns (U, sigma, Vh, sweeps) with a = U diag(sigma) Vh, sigma descending
+    (numpy), U and Vh CUDA tensors."""
+    import torch
+    if a.dtype != torch.complex128 or not a.is_cuda or a.dim() != 2:
+        raise ValueError("svd expects a 2-D complex128 CUDA tensor")
+    a = a.contiguous()
+    m, n = a.shape
+    k = min(m, n)
+    nbytes = C.c_size_t()
+    st = library().ttn_svd_workspace_size(m, n, C.byref(nbytes))
+    if st != TTN_OK:
+        raise TTNError(st, "ttn_svd_workspace_size")
+    ws = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=a.device)
+    base = (ws.data_ptr() + 255) // 256 * 256
+    U = torch.empty(m, k, dtype=torch.complex128, device=a.device)
+    Vh = torch.empty(k, n, dtype=torch.complex128, device=a.device)
+    sig = np.zeros(k, np.float64)
+    sweeps = C.c_int32()
+    st = library().ttn_svd(C.c_void_p(a.data_ptr()), m, n, C.c_void_p(U.data_ptr()), ptr(sig, C.c_double),
+                           C.c_void_p(Vh.data_ptr()), C.c_void_p(base), int(nbytes.value), float(wait_s),
+                           C.byref(sweeps), C.c_void_p(torch.cuda.current_stream(a.device).cuda_stream))
+    if st != TTN_OK:
+        raise TTNError(st, "ttn_svd")
+    return U, sig, Vh, int(sweeps.value)

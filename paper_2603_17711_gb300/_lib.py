@@ -29,7 +29,7 @@ class ttn_tree(C.Structure):
 class ttn_params(C.Structure):
     _fields_ = [("qr_tol", C.c_double), ("kappa", C.c_double), ("ps2_atol", C.c_double),
                 ("ps2_ratio", C.c_double), ("max_rank", C.c_int32), ("svd_tol", C.c_double),
-                ("max_split", C.c_int32), ("tensor_cores", C.c_int32)]
+                ("max_split", C.c_int32), ("tensor_cores", C.c_int32), ("wait_s", C.c_double)]
 
 
 DRIVE_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
@@ -65,6 +65,9 @@ SIGNATURES = [
     ("ttn_profile_read", C.c_int, [_h, C.c_int32, _f64p]),
     ("ttn_stats_reset", C.c_int, [_h]),
     ("ttn_autotune", C.c_int, [_h, C.c_int32]),
+    ("ttn_svd_workspace_size", C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    ("ttn_svd", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, _f64p, C.c_void_p, C.c_void_p, C.c_size_t,
+                          C.c_double, _i32p, C.c_void_p]),
     ("ttn_rdm_noalloc", C.c_int, [C.POINTER(ttn_tree), _i32p, _i32p, C.POINTER(C.c_void_p), C.c_void_p,
                                   C.c_void_p, C.c_char_p, C.c_size_t]),
     ("ttn_mlp_n_params", C.c_int, [_i32p]),

@@ -32,7 +32,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct ttn_ctx {
   Plan plan;
   int precision = TTN_FP64;
-  ttn_params params{1e-9, 2.5, 1e-7, 2.0, 32, 1e-12, kMaxSplit, 1};
+  ttn_params params{1e-9, 2.5, 1e-7, 2.0, 32, 1e-12, kMaxSplit, 1, 2.0};
   bool sop_loaded = false;
   bool ws_bound = false;
   bool envs_dirty = true;
@@ -66,6 +66,7 @@ struct ttn_ctx {
   double* svd_sigma = nullptr;
   int* svd_perm = nullptr;
   int* svd_info = nullptr;
+  unsigned* svd_sync = nullptr;  // barrier counters of the grid Jacobi SVD
   std::vector<double> discarded;  // discarded weight of every ps2 split (host log)
   std::vector<int> init_ranks;
   // learned rank proposer
@@ -91,11 +92,15 @@ struct ttn_ctx {
   // kernel accounting (ttn_stats / ttn_profile)
   int64_t n_launch[4] = {0, 0, 0, 0};
   double n_flops[4] = {0, 0, 0, 0};
-  bool profiling = false;
+  bool profiling = false;  // per-launch events (mode 1) or event nodes in the step graph (mode 2)
+  int prof_mode = 0;
+  bool capturing = false;   // inside ensure_graph's stream capture
+  int graph_prof = 0;       // prof_mode the current step graph was captured with
   struct Mark {
     int kind;
     cudaEvent_t a, b;
   };
+  static_assert(sizeof(Mark) > 0, "");
   std::vector<cudaEvent_t> ev_free;
   std::vector<Mark> marks;
   double prof_ms[4] = {0, 0, 0, 0};
@@ -123,6 +128,24 @@ struct ttn_ctx {
     if (graph_src) cudaGraphDestroy(graph_src);
     graph = nullptr;
     graph_src = nullptr;
+    for (auto& m : graph_marks) {
+      ev_free.push_back(m.a);
+      ev_free.push_back(m.b);
+    }
+    graph_marks.clear();
+  }
+  // event pairs recorded by every replay of the step graph (profile mode 2)
+  std::vector<struct Mark> graph_marks;
+  // after a replay: fold the graph's event pairs into prof_ms
+  cudaError_t read_graph_marks() {
+    if (graph_marks.empty()) return cudaSuccess;
+    cudaError_t err = cudaEventSynchronize(graph_marks.back().b);
+    if (err != cudaSuccess) return err;
+    for (auto& m : graph_marks) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) prof_ms[m.kind] += ms;
+    }
+    return cudaSuccess;
   }
 
   ~ttn_ctx() {
@@ -238,7 +261,7 @@ Layout layout_of(const Plan& p, int prec) {
   L.outs = take(p.ap_outs.size() * sizeof(ApOut));
   L.pjs = take(p.pj_outs.size() * sizeof(PjOut));
   L.drives = take(p.locals.size() * sizeof(DriveMat));
-  L.svd_small = take(p.theta_cap * sizeof(double) + (p.theta_cap + 4) * sizeof(int));
+  L.svd_small = take(p.theta_cap * sizeof(double) + (p.theta_cap + 4 + kSvdSyncInts) * sizeof(int));
   L.rsvd = take(3 * p.theta_cap * sizeof(double2));
   L.mlp = take((24 + 13 + mlp_ws_floats(1) + 8) * sizeof(float) + 2 * sizeof(double));
   L.flag = take(sizeof(int) * 4);
@@ -285,11 +308,18 @@ struct Exec {
   void run(int kind, double flops, F&& launch) {
     h->n_launch[kind] += 1;
     h->n_flops[kind] += flops;
-    if (!h->profiling) {
+    if (h->prof_mode == 0) {
       launch();
       return;
     }
     cudaEvent_t a = h->get_event(), b = h->get_event();
+    if (h->capturing) {  // profile mode 2: event-record nodes inside the step graph
+      cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+      launch();
+      cudaEventRecordWithFlags(b, s, cudaEventRecordExternal);
+      h->graph_marks.push_back({kind, a, b});
+      return;
+    }
     cudaEventRecord(a, s);
     launch();
     cudaEventRecord(b, s);
@@ -440,6 +470,49 @@ struct Exec {
   void note(cudaError_t e) {
     if (e != cudaSuccess && err == cudaSuccess) err = e;
   }
+  // a failure found on the host during a ps2 split (SVD not converged, a grid
+  // wait that gave up): the split is abandoned and ttn_step returns it
+  ttn_status fail_st = TTN_OK;
+  std::string fail_msg;
+  void fail(ttn_status st, const std::string& m) {
+    if (fail_st == TTN_OK) {
+      fail_st = st;
+      fail_msg = m;
+    }
+  }
+  uint64_t wait_ns() const { return (uint64_t)(h->params.wait_s * 1e9); }
+  // launch the Jacobi SVD (one CTA or the whole GPU) and read back sigma; false
+  // (with fail_st set) when it did not converge or a grid wait gave up
+  bool jacobi(const double2* theta, int m, int n, std::vector<double>& sig) {
+    const int nc = std::min(m, n);
+    run(2, 0.0, [&] {
+      if (!launch_jacobi_svd_grid(theta, m, n, h->svd_A, h->svd_V, h->svd_sigma, h->svd_info, h->svd_sync,
+                                  h->flag_dev, wait_ns(), s))
+        {
+          const cudaError_t e = cudaGetLastError();
+          note(e != cudaSuccess ? e : cudaErrorLaunchFailure);
+        }
+    });
+    sig.assign(nc, 0.0);
+    int info[2] = {0, 0}, flag = 0;
+    note(cudaMemcpyAsync(sig.data(), h->svd_sigma, nc * sizeof(double), cudaMemcpyDeviceToHost, s));
+    note(cudaMemcpyAsync(info, h->svd_info, sizeof(info), cudaMemcpyDeviceToHost, s));
+    note(cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    note(cudaStreamSynchronize(s));
+    if (err != cudaSuccess) return false;
+    if (flag & 16) {
+      fail(TTN_ETIMEOUT, "a grid barrier of the Jacobi SVD gave up after wait_s");
+      return false;
+    }
+    if (info[0] >= kJacMaxSweeps) {
+      fail(TTN_ENUMERIC, "Jacobi SVD of a " + std::to_string(m) + " x " + std::to_string(n) +
+                             " two-site matrix did not converge in " + std::to_string(kJacMaxSweeps) + " sweeps");
+      return false;
+    }
+    const int nr = std::max(m, n);
+    h->n_flops[2] += 8.0 * 4.0 * info[0] * 0.5 * nc * (nc - 1) * (double)(nr + nc);
+    return true;
+  }
   // new dims -> job lists rebuilt on the host and re-uploaded (queued kernels
   // still read the old tables, so the stream is drained first)
   void upload_jobs() {
@@ -458,7 +531,7 @@ struct Exec {
     upload_jobs();
   }
   void two_site(int first, int second, double hh, int centre_to) {
-    if (err != cudaSuccess) return;
+    if (err != cudaSuccess || fail_st != TTN_OK) return;
     const int lf = p.tree.leg_index(first, second), ls = p.tree.leg_index(second, first);
     const int fd[3] = {p.dims[first][0], p.dims[first][1], p.dims[first][2]};
     const int sd[3] = {p.dims[second][0], p.dims[second][1], p.dims[second][2]};
@@ -469,7 +542,7 @@ struct Exec {
       launch_merge(h->h_bufs[first], fd, lf, h->h_bufs[second], sd, ls, h->h_bufs[tl], lo_copy(tl), s);
     });
     rk4(p.two_site[p.dir_id(first, second)], tl, p.buf.th_ys, p.buf.th_ys2, p.buf.th_acc, hh);
-    const int nc = std::min(m, n), nr = std::max(m, n);
+    const int nc = std::min(m, n);
     const int child = p.tree.parent[first] == second ? first : second;
     const int r_cur = p.ranks[child];
     const int cap = std::min(h->params.max_rank, nc);
@@ -508,16 +581,15 @@ struct Exec {
       if (kk < nc && err == cudaSuccess) {
         run(3, 0.0, [&] { launch_gauss(h->rs_omega, (int64_t)n * kk, 0x5eedull + 7919ull * h->n_splits, s); });
         run(2, 8.0 * m * n * kk, [&] { launch_zgemm(h->h_bufs[tl], h->rs_omega, h->rs_Y, m, kk, n, false, s); });
-        run(2, 0.0, [&] {
+        run(2, 16.0 * (2.0 * m * kk * kk - 2.0 * kk * kk * kk / 3.0), [&] {
           launch_qr(h->rs_Y, m, 1, kk, 2, h->params.qr_tol, h->qr_work, h->qr_elems, h->h_bufs[p.buf.tmp], h->svd_V, h->flag_dev,
                     nullptr, nullptr, s);
         });
         run(2, 8.0 * m * n * kk, [&] { launch_zgemm(h->rs_Y, h->h_bufs[tl], h->rs_B, kk, n, m, true, s); });
-        run(2, 0.0, [&] { launch_jacobi_svd(h->rs_B, kk, n, h->svd_A, h->svd_V, h->svd_sigma, h->svd_info, s); });
         run(3, 0.0, [&] { launch_norm2(h->h_bufs[tl], (int64_t)m * n, h->rs_norm, s); });
-        std::vector<double> sb(kk);
+        std::vector<double> sb;
+        if (!jacobi(h->rs_B, kk, n, sb)) return;
         double tot = 0.0;
-        note(cudaMemcpyAsync(sb.data(), h->svd_sigma, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
         note(cudaMemcpyAsync(&tot, h->rs_norm, sizeof(double), cudaMemcpyDeviceToHost, s));
         note(cudaStreamSynchronize(s));
         std::vector<int> pb(kk);
@@ -548,16 +620,7 @@ struct Exec {
       }
     }
     if (!accepted) {
-      run(2, 0.0, [&] {
-        launch_jacobi_svd(h->h_bufs[tl], m, n, h->svd_A, h->svd_V, h->svd_sigma, h->svd_info, s);
-      });
-      sig.assign(nc, 0.0);
-      int info[2] = {0, 0};
-      note(cudaMemcpyAsync(sig.data(), h->svd_sigma, nc * sizeof(double), cudaMemcpyDeviceToHost, s));
-      note(cudaMemcpyAsync(info, h->svd_info, sizeof(info), cudaMemcpyDeviceToHost, s));
-      note(cudaStreamSynchronize(s));
-      if (err != cudaSuccess) return;
-      h->n_flops[2] += 8.0 * 4.0 * info[0] * 0.5 * nc * (nc - 1) * (double)(nr + nc);
+      if (!jacobi(h->h_bufs[tl], m, n, sig)) return;
       // truncation (host): r0 = #{sigma > ps2_atol}, r = min(cap, max(1, ceil(ratio r0)))
       perm.resize(nc);
       for (int i = 0; i < nc; ++i) perm[i] = i;
@@ -663,9 +726,10 @@ struct Exec {
 // Capture one ps1 step of h as a CUDA graph (autonomous generator, non-default
 // stream, not profiling). Returns whether h->graph is usable for dt.
 bool ensure_graph(ttn_t h, double dt) {
-  const bool graphable = h->plan.n_drives == 0 && !h->profiling && h->stream != nullptr && !h->graph_disabled;
+  const bool graphable =
+      h->plan.n_drives == 0 && h->prof_mode != 1 && h->stream != nullptr && !h->graph_disabled;
   if (!graphable) return false;
-  if (h->graph && h->graph_dt == dt) return true;
+  if (h->graph && h->graph_dt == dt && h->graph_prof == h->prof_mode) return true;
   h->drop_graph();
   Exec ex(h);
   int64_t l0[4];
@@ -677,7 +741,9 @@ bool ensure_graph(ttn_t h, double dt) {
   cudaGraph_t g = nullptr;
   bool ok = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   if (ok) {
+    h->capturing = h->prof_mode == 2;
     ex.step_ps1(dt, h->t);
+    h->capturing = false;
     ok = cudaStreamEndCapture(h->stream, &g) == cudaSuccess && g != nullptr;
   }
   if (ok) ok = cudaGraphInstantiate(&h->graph, g, 0) == cudaSuccess;
@@ -696,6 +762,7 @@ bool ensure_graph(ttn_t h, double dt) {
   }
   h->graph_src = g;
   h->graph_dt = dt;
+  h->graph_prof = h->prof_mode;
   return true;
 }
 
@@ -814,7 +881,7 @@ ttn_status ttn_set_params(ttn_t h, const ttn_params* prm) {
     if (!prm) return h->fail(TTN_EINVAL, "null params");
     if (!(prm->qr_tol >= 0) || !(prm->kappa > 0) || !(prm->ps2_atol >= 0) || !(prm->ps2_ratio >= 1) ||
         prm->max_rank < 1 || !(prm->svd_tol >= 0) || prm->max_split < 1 || prm->max_split > kMaxSplit ||
-        (prm->tensor_cores != 0 && prm->tensor_cores != 1))
+        (prm->tensor_cores != 0 && prm->tensor_cores != 1) || !(prm->wait_s >= 0.0 && prm->wait_s <= 60.0))
       return h->fail(TTN_EINVAL, "parameter out of range");
     if (h->ws_bound && prm->max_rank != h->params.max_rank)
       return h->fail(TTN_ESTATE, "max_rank must be set before the workspace is bound");
@@ -941,6 +1008,7 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
     h->svd_sigma = (double*)(base + L.svd_small);
     h->svd_perm = (int*)(h->svd_sigma + p.theta_cap);
     h->svd_info = h->svd_perm + p.theta_cap;
+    h->svd_sync = (unsigned*)(h->svd_info + 4);
     h->rs_omega = (double2*)(base + L.rsvd);
     h->rs_Y = h->rs_omega + p.theta_cap;
     h->rs_B = h->rs_Y + p.theta_cap;
@@ -1123,6 +1191,7 @@ ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
       for (int k = 0; k < n_steps; ++k) {
         ex.step_ps2(dt, h->t);
         if (ex.err != cudaSuccess) return cuda_fail(h, ex.err, "ps2 step");
+        if (ex.fail_st != TTN_OK) return h->fail(ex.fail_st, ex.fail_msg);
         h->t += dt;
       }
       ex.run(3, 0.0, [&] { launch_check_finite(h->h_bufs[0], h->plan.P[0], h->flag_dev, h->stream); });
@@ -1139,6 +1208,7 @@ ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
     if (graphable && h->graph) {
       for (; k < n_steps; ++k) {
         CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+        if (h->graph_prof == 2) CUDA_TRY(h, h->read_graph_marks());
         for (int c = 0; c < 4; ++c) {
           h->n_launch[c] += h->graph_launch[c];
           h->n_flops[c] += h->graph_flops[c];
@@ -1162,6 +1232,7 @@ static ttn_status check_flag(ttn_t h) {
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   if (flag & 2) return h->fail(TTN_ETIMEOUT, "a cluster or grid exchange of the QR kernels gave up after 2 s");
   if (flag & 8) return h->fail(TTN_ETIMEOUT, "a tensor-core MMA wait gave up after 1 s");
+  if (flag & 16) return h->fail(TTN_ETIMEOUT, "a grid barrier of the Jacobi SVD gave up after wait_s");
   if (flag) return h->fail(TTN_ENUMERIC, "non-finite amplitude in the root tensor");
   return TTN_OK;
 }
@@ -1259,7 +1330,7 @@ ttn_status ttn_batch_step(ttn_t* hs, int32_t n, double dt, int32_t scheme, int32
       ttn_status st = ensure_envs(hs[i]);
       if (st != TTN_OK) return h0->fail(st, std::string("batch member: ") + hs[i]->err);
       if (hs[i]->plan.n_sub(dt, hs[i]->params.kappa) > (1 << 20)) return h0->fail(TTN_EINVAL, "dt too large");
-      all_graphs = ensure_graph(hs[i], dt);
+      all_graphs = hs[i]->prof_mode == 0 && ensure_graph(hs[i], dt);
     }
     if (!all_graphs) {  // drives, default streams or profiling: one handle after another
       for (int i = 0; i < n; ++i) {
@@ -1334,7 +1405,9 @@ ttn_status ttn_stats(ttn_t h, int32_t kind, int64_t* launches, double* flops) {
 
 ttn_status ttn_profile(ttn_t h, int32_t on) {
   if (!h) return TTN_EINVAL;
-  h->profiling = on != 0;
+  if (on < 0 || on > 2) return TTN_EINVAL;
+  h->prof_mode = on;
+  h->profiling = on == 1;
   return TTN_OK;
 }
 

@@ -152,6 +152,29 @@ void launch_merge(const double2* Uf, const int* fd, int lf, const double2* Us, c
 // sigma: min(m,n) (unsorted), info[0] = sweeps, info[1] = 1 if Theta^H was used.
 void launch_jacobi_svd(const double2* theta, int m, int n, double2* A, double2* V, double* sigma, int* info,
                        cudaStream_t s);
+// Convergence threshold of both Jacobi kernels: |x^H y| > tol |x| |y| rotates,
+// tol = 2 sqrt(max(rows, 64)) DBL_EPSILON (above the rounding noise of the
+// summed Gram entries); a run that reaches kJacMaxSweeps is not converged.
+double jacobi_tol(int m, int n);
+// A column whose squared norm is at most 16 rows eps^2 ||A||_F^2 is rounding
+// noise of the matrix (an exactly dependent column leaves one after its
+// rotation); rotating it against the others would go on forever, each rotation
+// only shrinking the noise. Such pairs are not rotated: the singular values
+// they leave are below sqrt(16 rows) eps ||A||_F, far under the svd_tol
+// cut that replaces them by the deterministic completion.
+__host__ __device__ inline double jacobi_negligible(int rows, double fro2) {
+  return 16.0 * rows * 2.220446049250313e-16 * 2.220446049250313e-16 * fro2;
+}
+constexpr int kJacMaxSweeps = 60;
+// The same SVD over the whole GPU (svd.cu): pairs of a circle-method round dealt
+// to the CTAs of one cooperative launch, one grid barrier per round. Used when
+// the smaller side has at least kJacGridMinCols columns (else the one-CTA
+// kernel). sync: kSvdSyncInts device ints (cleared by the launch); a grid wait
+// longer than wait_ns sets bit 4 (16) of *flag. Same outputs as launch_jacobi_svd.
+constexpr int kJacGridMinCols = 24;
+constexpr int kSvdSyncInts = 128;
+bool launch_jacobi_svd_grid(const double2* theta, int m, int n, double2* A, double2* V, double* sigma, int* info,
+                            unsigned* sync, int* flag, uint64_t wait_ns, cudaStream_t s);
 void launch_svd_vecs(const double2* A, const double2* V, const double* sigma, int m, int n, const int* perm, int r,
                      int g, bool iso_first, double2* Z, double2* Zg, double2* Cm, cudaStream_t s);
 void launch_restore_cols(double2* Z, const double2* Zg, int rows, int r, int g, cudaStream_t s);

@@ -28,7 +28,10 @@ namespace {
 constexpr int64_t kRdmScratchComplex = 65536;  // 1 MiB of double2
 static __device__ __align__(256) double2 g_rdm_scratch[kRdmScratchComplex];
 
-// Device address of g_rdm_scratch, looked up once per device.
+// Device address of g_rdm_scratch, looked up once per device and kept for the
+// life of the process: after cudaDeviceReset (which unloads the module) the
+// cached address is stale, so a process that resets a device must not call
+// ttn_rdm_noalloc on it again.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double2* g_scratch_ptr[kMaxDevices] = {nullptr};
@@ -77,9 +80,14 @@ extern "C" ttn_status ttn_rdm_noalloc(const ttn_tree* tree, const int32_t* leg_d
     }
   int dev = 0;
   cudaError_t ce = cudaGetDevice(&dev);
-  if (ce != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  if (ce != cudaSuccess) {
     set_err(err, err_len, std::string("cudaGetDevice: ") + cudaGetErrorString(ce));
     return TTN_ECUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_err(err, err_len, "ttn_rdm_noalloc: device ordinal " + std::to_string(dev) + " is beyond the " +
+                              std::to_string(kMaxDevices) + " devices it keeps a scratch address for");
+    return TTN_EINVAL;
   }
   double2* scratch = nullptr;
   {

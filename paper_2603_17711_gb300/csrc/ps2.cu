@@ -83,6 +83,19 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(const double2* theta, in
   for (int64_t k = tid; k < (int64_t)nc * nc; k += blockDim.x)
     V[k] = make_double2((k % nc) == (k / nc) ? 1.0 : 0.0, 0.0);
   __syncthreads();
+  // ||A||_F^2 (fixed-order sums): columns at the rounding floor of the matrix
+  // are not rotated (see jacobi_negligible)
+  __shared__ double s_fro[kJacThreads / 32];
+  {
+    double f = 0.0;
+    for (int64_t k = tid; k < (int64_t)nr * nc; k += blockDim.x) f += A[k].x * A[k].x + A[k].y * A[k].y;
+    f = ws(f);
+    if (lane == 0) s_fro[wid] = f;
+    __syncthreads();
+  }
+  double fro2 = 0.0;
+  for (int w = 0; w < nw; ++w) fro2 += s_fro[w];
+  const double tiny2 = jacobi_negligible(nr, fro2);
   const int N = nc + (nc & 1);
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
@@ -119,7 +132,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(const double2* theta, in
         cr = ws(cr);
         ci = ws(ci);
         const double ac = sqrt(cr * cr + ci * ci);
-        if (!(ac > tol * sqrt(a * b)) || ac == 0.0) continue;
+        if (!(ac > tol * sqrt(a * b)) || ac == 0.0 || !(fmin(a, b) > tiny2)) continue;
         const double zeta = (b - a) / (2.0 * ac);
         const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
@@ -159,7 +172,7 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(const double2* theta, in
 
 void launch_jacobi_svd(const double2* theta, int m, int n, double2* A, double2* V, double* sigma, int* info,
                        cudaStream_t s) {
-  k_jacobi<<<1, kJacThreads, 0, s>>>(theta, m, n, A, V, sigma, info, 1e-15, 60);
+  k_jacobi<<<1, kJacThreads, 0, s>>>(theta, m, n, A, V, sigma, info, jacobi_tol(m, n), kJacMaxSweeps);
 }
 
 // Z (rows_iso x r, row-major) and the centre factor Cm (row-major: first side

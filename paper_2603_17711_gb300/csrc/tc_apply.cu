@@ -350,6 +350,11 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
   const uint64_t deadline = gtimer() + 1000000000ull;
   bool ok = true;
   uint32_t ph[2] = {0u, 0u}, lph[2] = {0u, 0u};
+  // asynchronous operations thread 0 issued and nobody has waited for yet: the
+  // MMA commit of each stage and the bulk copy into each stage. A wait that
+  // gives up stops thread 0 from issuing more; before the CTA frees its tensor
+  // memory and leaves, thread 0 waits (bounded again) for whatever is pending.
+  bool pend_m[2] = {false, false}, pend_l[2] = {false, false};
 
   // chunk ci -> (operator, tensor, K chunk); poff: pre-split operator offset or -1
   auto chunk_src = [&](int ci, const float2*& M, const float2*& X, int& kc, int64_t& poff) {
@@ -378,6 +383,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
   };
   // A chunk by one bulk copy from the pre-split pool (thread 0 issues it)
   auto bulk_a = [&](float* buf, int64_t poff, int kc, int b) {
+    pend_l[b] = true;
     if (tid == 0) {
       const uint32_t bytes = 2u * kAElems * 4u;
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&lbar[b])), "r"(bytes)
@@ -423,7 +429,10 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
     // make the staged operands visible to the tensor core, then issue
     if (bulk[b] && ok) {
       ok = mbar_wait(&lbar[b], lph[b], deadline);
-      lph[b] ^= 1u;
+      if (ok) {
+        lph[b] ^= 1u;
+        pend_l[b] = false;
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -447,13 +456,17 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        smem_u32(&mbar[b]))
                    : "memory");
+      pend_m[b] = true;
     }
     if (ci + 2 < nchunks) fetch(ci + 2, Rld, b);
     if (ci + 1 < nchunks) {
       // the other stage is free once the MMAs of chunk ci-1 have completed
       if (ci >= 1 && ok) {
         ok = mbar_wait(&mbar[b ^ 1], ph[b ^ 1], deadline);
-        ph[b ^ 1] ^= 1u;
+        if (ok) {
+          ph[b ^ 1] ^= 1u;
+          pend_m[b ^ 1] = false;
+        }
       }
       if (bulk[b ^ 1] && ok) bulk_a(tsm + (b ^ 1) * kStageFloats, poffs[b ^ 1], kcs[b ^ 1], b ^ 1);
       store_chunk(tsm + (b ^ 1) * kStageFloats, Rst, leg == 2, !bulk[b ^ 1]);
@@ -467,9 +480,19 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
   if (ok) {
     const bool odd = ((nchunks - 1) & 1) != 0;
     ok = mbar_wait(odd ? &mbar[1] : &mbar[0], odd ? ph[1] : ph[0], deadline);
+    if (ok) pend_m[odd ? 1 : 0] = false;
   }
   ok = __syncthreads_and(ok) != 0;  // CTA-uniform: tcgen05.ld below is warp-collective
-  if (!ok && tid == 0) atomicOr(flag, 8);
+  if (!ok && tid == 0) {
+    atomicOr(flag, 8);
+    // drain: no MMA may still write tensor memory, and no bulk copy may still
+    // land in shared memory, once the CTA deallocates and exits
+    const uint64_t drain = gtimer() + 1000000000ull;
+    for (int b = 0; b < 2; ++b) {
+      if (pend_m[b]) mbar_wait(&mbar[b], ph[b], drain);
+      if (pend_l[b]) mbar_wait(&lbar[b], lph[b], drain);
+    }
+  }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // tensor memory -> shared (rows = embedded output rows, 64 columns)
   float* Ds = tsm;  // [128][65]

@@ -75,8 +75,10 @@ def test_trained_proposer_gain(pkg):
     """Train on splits logged by GPU ps2 runs of one workload family, then run a
     fresh workload with and without the network: the proposals are accepted for
     most splits (each accepted split replaces the full Jacobi SVD of Theta by a
-    sketch of rank r+8), the QR/SVD kernel time drops, and rho_S stays within
-    1e-8 of the run without the network and of the oracle."""
+    sketch of rank r+8), the QR/SVD arithmetic drops (FLOPs counted on the host
+    from the launched shapes and the sweeps each Jacobi SVD ran, so the check
+    does not depend on timing; the kernel times are printed), and rho_S stays
+    within 1e-8 of the run without the network and of the oracle."""
     train_w = [W.spin_boson_tt(depth=6, n_pade=4, rank=2, tree="btt"),
                W.spin_boson_tt(depth=5, n_pade=5, rank=3, tree="btt")]
     feats, labels = [], []
@@ -100,10 +102,13 @@ def test_trained_proposer_gain(pkg):
     o = ottn.from_workload(w, params=ottn.Params(ps2_atol=1e-7, max_rank=16))
     for _ in range(12):
         o.step(w.dt, "ps2")
-    print(f"proposed {proposed} accepted {accepted}; QR+SVD kernel ms without {svd0:.2f} with {svd1:.2f}; "
+    _, flops0 = g0.ttn_stats(2)
+    _, flops1 = g1.ttn_stats(2)
+    print(f"proposed {proposed} accepted {accepted}; QR+SVD GFLOP without {flops0 / 1e9:.3f} with "
+          f"{flops1 / 1e9:.3f}; kernel ms without {svd0:.2f} with {svd1:.2f}; "
           f"wall s without {wall0:.3f} with {wall1:.3f}")
     assert accepted >= 0.5 * proposed
-    assert svd1 < svd0
+    assert flops1 < flops0
     assert np.max(np.abs(rho1 - rho0)) <= 1e-8
     assert np.max(np.abs(rho0 - o.rdm())) <= 1e-10
     assert np.max(np.abs(rho1 - o.rdm())) <= 1e-8
