@@ -76,8 +76,9 @@ print(json.dumps({{"steps": n, "seconds": el, "rho": [[[z.real, z.imag] for z in
 """
 
 
-def run_oracle(budget_s: float, max_steps: int) -> dict:
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+def run_oracle(budget_s: float, max_steps: int, threads: int = 1) -> dict:
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t,
                CUDA_VISIBLE_DEVICES="")
     code = ORACLE_SNIPPET.format(root=ROOT, budget=budget_s, max_steps=max_steps)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
@@ -265,6 +266,145 @@ def accuracy_leg(args, pkg, torch, w, local_rank):
     return out
 
 
+def measure_peaks(torch, dev) -> dict:
+    """Dense matmul rates of this GPU measured in this run (torch.matmul, CUDA
+    events, best of `reps` after one warm-up): FP64 (4096^3), FP32 on the CUDA
+    cores (TF32 off, 8192^3), TF32 tensor cores (8192^3) and BF16 (8192^3),
+    2 n^3 FLOP per product. They are the roofline denominators of the pipes the
+    kernels use (FP64: the node contractions of the FP64 form; FP32: the mixed
+    form on the CUDA cores; TF32: its tensor-core contractions)."""
+    out = {}
+    old = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for name, dtype, n, tf32, reps in (("fp64", torch.float64, 4096, False, 5),
+                                          ("fp32_simt", torch.float32, 8192, False, 5),
+                                          ("tf32", torch.float32, 8192, True, 10),
+                                          ("bf16", torch.bfloat16, 8192, False, 10)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device=dev).to(dtype)
+            b = torch.randn(n, n, device=dev).to(dtype)
+            torch.matmul(a, b)
+            torch.cuda.synchronize()
+            best = None
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[name + "_tflops"] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = old
+    torch.cuda.empty_cache()
+    out["how"] = "torch.matmul best of 5-10 (CUDA events) in this run: FP64 4096^3, FP32 (TF32 off) / TF32 / BF16 8192^3"
+    return out
+
+
+def config1_leg(pkg, torch, local_rank, flush) -> dict:
+    """Spin-boson tensor train (H = 0.5 sz + sx, Drude lambda 0.5, omega_c 1,
+    beta 1, 1 Drude + 3 Pade features, depth 10, rank 10, dt 0.01), 1000 ps1
+    steps in FP64: steps/s of the graph-replayed step and rho_S against the
+    stored oracle trajectory (every 10th step)."""
+    w = W.spin_boson_tt(n_steps=1000)
+    rows = np.loadtxt(os.path.join(ROOT, "tests", "golden", "spin_boson_tt_k4_n10_r10.txt"))
+    g = make_gpu(pkg, w, local_rank)
+    err = float(np.max(np.abs(g.ttn_rdm().reshape(-1) - (rows[0, 1::2] + 1j * rows[0, 2::2]))))
+    for r in rows[1:]:
+        g.ttn_step(w.dt, 1, int(r[0]) - int(round(g.ttn_time() / w.dt)))
+        err = max(err, float(np.max(np.abs(g.ttn_rdm().reshape(-1) - (r[1::2] + 1j * r[2::2])))))
+    g.close()
+    g = make_gpu(pkg, w, local_rank)
+    g.ttn_step(w.dt, 1, 3)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(g.stream):
+        flush.zero_()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(g.stream)
+    g.ttn_step(w.dt, 1, 1000)
+    b.record(g.stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    g.close()
+    return {"workload": "spin-boson tensor train: K = 4 (1 Drude + 3 Pade), depth 10, rank 10, 4 nodes, ps1 FP64, "
+                        "dt 0.01, 1000 steps", "steps_per_s": 1000 / (ms * 1e-3), "ms_per_step": ms / 1000,
+            "rdm_max_abs_vs_stored_oracle": err, "steps_compared": int(rows[-1, 0]),
+            "l2": "state L2-resident (39 kB): one flush before the 1000 steps"}
+
+
+def ps2_leg(args, pkg, torch, local_rank) -> dict:
+    """Adaptive rank (ps2) on the driven two-level system with the structured
+    bath (Drude + three Brownian peaks + Pade features, depth 10, binary tree,
+    ps2_atol 1e-6, ratio 2), the plain SVD rule against the learned rank
+    proposer. The network is trained on the GPU (the library's forward,
+    backward and Adam kernels) on the split records of rule runs of two other
+    bath sizes, then both forms run the same window."""
+    cap, npd, n = args.ps2_cap, args.ps2_pade, args.ps2_steps
+    leg_t0 = time.perf_counter()
+
+    def run(w, net=None, record=False, steps=None):
+        nn = n if steps is None else steps
+        g = pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0, drives=w.drives,
+                           params={"max_rank": cap, "ps2_atol": w.ps2_atol}, device=local_rank)
+        if net is not None:
+            g.ttn_set_rank_proposer(net)
+        g.ttn_stats_reset()
+        rhos, ranks = [], []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(nn):
+            g.ttn_step(w.dt, pkg.TTN_PS2, 1)
+            rhos.append(g.ttn_rdm())
+            if record and (k + 1) % max(1, nn // 10) == 0:
+                ranks.append([k + 1, int(max(g.ttn_get_ranks()))])
+        el = time.perf_counter() - t0
+        prop = g.ttn_proposer_stats()
+        fl = g.ttn_stats(2)[1]
+        return g, np.array(rhos), el, ranks, prop, fl
+
+    # training records from rule runs of other bath sizes (same family)
+    feats, labels = [], []
+    n_train = min(n, 40)
+    for tp in (max(0, npd - 2), npd + 1):
+        wt = W.driven_structured_tls(n_pade=tp, depth=10, cap=cap)
+        g, _, _, _, _, _ = run(wt, steps=n_train)
+        f, y = g.ttn_split_log()
+        feats.append(f)
+        labels.append(y)
+        g.close()
+    feats, labels = np.concatenate(feats), np.concatenate(labels)
+    net = pkg.RankProposer(seed=1, device=local_rank)
+    t0 = time.perf_counter()
+    hist = net.train(feats, labels, steps=400, lr=3e-3)
+    train_s = time.perf_counter() - t0
+    acc = float(np.mean(net.forward(feats).argmax(1).cpu().numpy() == labels))
+
+    w = W.driven_structured_tls(n_pade=npd, depth=10, cap=cap)
+    g0, r0, el0, ranks0, _, fl0 = run(w, record=True)
+    n_splits = len(g0.ttn_split_log()[1])
+    g1, r1, el1, ranks1, (proposed, accepted), fl1 = run(w, net, record=True)
+    g0.close()
+    g1.close()
+    return {"workload": f"driven TLS, structured bath: K = {w.K} (1 Drude + 6 Brownian + {npd} Pade), depth 10, "
+                        f"binary tree ({len(w.parent)} nodes), ps2 atol 1e-6 ratio 2 cap {cap}, dt 0.01, {n} steps",
+            "svd_rule": {"steps_per_s": n / el0, "qr_svd_gflop": fl0 / 1e9, "splits": n_splits,
+                         "max_rank_trajectory": ranks0},
+            "learned": {"steps_per_s": n / el1, "qr_svd_gflop": fl1 / 1e9, "splits_proposed": proposed,
+                        "splits_accepted": accepted,
+                        "fraction_skipping_full_svd": accepted / proposed if proposed else 0.0,
+                        "max_rank_trajectory": ranks1,
+                        "training": {"records": int(len(labels)), "steps": 400, "loss_first_last": [hist[0], hist[-1]],
+                                     "train_accuracy": acc, "seconds": train_s,
+                                     "source": f"rule runs of the same family with {max(0, npd - 2)} and {npd + 1} "
+                                               f"Pade features, {n_train} steps each"}},
+            "speedup_learned_vs_rule": el0 / el1,
+            "rdm_max_abs_learned_vs_rule": float(np.max(np.abs(r1 - r0))),
+            "timing": "host wall clock (ps2 synchronises at every split)",
+            "leg_seconds": time.perf_counter() - leg_t0}
+
+
 def bench_ours(args, rank, world, local_rank):
     import torch
     import paper_2603_17711_gb300 as pkg
@@ -278,6 +418,10 @@ def bench_ours(args, rank, world, local_rank):
     if args.accuracy_steps:  # long trajectory: mixed against FP64 on the GPU, step by step
         if rank == 0:
             print(json.dumps({"accuracy": accuracy_leg(args, pkg, torch, w, local_rank)}), flush=True)
+        return
+    if args.ps2_only:  # only the adaptive-rank leg
+        if rank == 0:
+            print(json.dumps({"ps2_learned_rank": ps2_leg(args, pkg, torch, local_rank)}), flush=True)
         return
     if args.rank64_only:  # profiling aid: only the rank-64 leg, in the form asked for
         forms = (("fp64", 0),) if args.rank64_only == "fp64" else (("mixed_fp32", pkg.TTN_MIXED_FP32),)
@@ -311,10 +455,11 @@ def bench_ours(args, rank, world, local_rank):
     flops = {k: g.ttn_stats(k)[1] for k in range(4)}
     ms_max = replica_max(ms, dist, dev)
 
-    # ---- per-kernel-class device time (roofline of the dominant kernel) ----
+    # ---- per-kernel-class device time (roofline of the dominant kernel), taken
+    # from event-record nodes inside the same replayed step graph ----
     g.ttn_stats_reset()
-    g.ttn_profile(True)
-    timed_steps(torch, g, w, args.steps, flush)
+    g.ttn_profile(2)
+    ms_prof = timed_steps(torch, g, w, args.steps, flush)
     g.ttn_profile(False)
     prof = {k: (g.ttn_stats(k)[0], g.ttn_stats(k)[1], g.ttn_profile_read(k)) for k in range(4)}
     rho_gpu_final = g.ttn_rdm()
@@ -331,7 +476,7 @@ def bench_ours(args, rank, world, local_rank):
     ms_mixed = timed_steps(torch, gm, w, args.steps, flush)
     mixed_flops = gm.ttn_stats(0)[1]
     gm.ttn_stats_reset()
-    gm.ttn_profile(True)
+    gm.ttn_profile(2)
     timed_steps(torch, gm, w, args.steps, flush)
     gm.ttn_profile(False)
     prof_m = {k: (gm.ttn_stats(k)[0], gm.ttn_stats(k)[1], gm.ttn_profile_read(k)) for k in range(4)}
@@ -350,6 +495,10 @@ def bench_ours(args, rank, world, local_rank):
 
     # ---- precision workload: the same chain at bond rank 64 (QRs up to 4096 x 64) ----
     r64 = None if args.no_rank64 else rank64_leg(args, pkg, torch, flush, local_rank)
+    # ---- the spin-boson tensor train, 1000 steps against the stored oracle trajectory ----
+    c1 = config1_leg(pkg, torch, local_rank, flush)
+    # ---- adaptive rank: SVD rule against the learned rank proposer ----
+    p2 = None if args.no_ps2 else ps2_leg(args, pkg, torch, local_rank)
 
     # ---- batched: 256 uneven spin-boson instances in one graph launch per step ----
     batch_out = None
@@ -410,8 +559,7 @@ def bench_ours(args, rank, world, local_rank):
                                     "ms_per_batched_step": ms_bm / args.steps,
                                     "rdm_max_abs_vs_fp64_batch": max(errs),
                                     "rdm_max_rel_vs_fp64_batch": max(e / max(1.0, sc) for e, sc in zip(errs, scale)),
-                                    "rdm_max_abs_vs_fp64_batch_physical": max(bounded) if bounded else None,
-                                    "instances_outside_physical_range": len(errs) - len(bounded),
+                                    "instances_with_max_abs_rho_above_1": len(errs) - len(bounded),
                                     "steps_compared": args.warmup + args.steps},
                      "l2": "one 256 MB flush before the timed batch (the 256 states total ~0.3 GB)"}
 
@@ -428,13 +576,22 @@ def bench_ours(args, rank, world, local_rank):
     h2d = sum(np.asarray(v).nbytes for v in sop.values()) + w.rho0.nbytes
     g2.close()
     e2e_s = replica_max(e2e_s, dist, dev)
+    peaks = measure_peaks(torch, dev)
 
     if rank != 0:
         return
     names = {0: "node/bond application (k_apply)", 1: "environment update", 2: "Householder QR", 3: "other"}
     dom = max(range(4), key=lambda k: prof[k][2])
     n_l, fl, t_ms = prof[dom]
-    achieved = fl / (t_ms * 1e-3) / 1e12 if t_ms > 0 else 0.0
+    # the class's share of the summed device time of the replayed step graph
+    # (event-record nodes) times the step time of the unprofiled timed run:
+    # gaps between kernels are attributed in proportion, so this is a lower
+    # bound of the kernels' own rate
+    prof_sum = sum(p[2] for p in prof.values())
+    share = {k: prof[k][2] / prof_sum for k in range(4)} if prof_sum > 0 else {k: 0.0 for k in range(4)}
+    t_dom = share[dom] * ms_max
+    achieved = (fl / args.steps) / (share[dom] * (ms_max / args.steps) * 1e-3) / 1e12 if share[dom] > 0 else 0.0
+    fp64_peak = peaks["fp64_tflops"]
     k1_launches, k1_flops, k1_ms = prof[0]
     value = replicas_value(world, args.steps, ms_max)
     out = {
@@ -447,17 +604,25 @@ def bench_ours(args, rank, world, local_rank):
                    "launch_shapes": "autotuned (ttn_autotune, %.2f s before the warm-up)" % tune_s
                    if tune_s is not None else "built-in rule"},
         "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                      "traffic": APPLY_DRAM_BYTES if names[dom].startswith("node/bond") else None,
                      "traffic_source": "mean dram__bytes_read+write per k_apply launch, ncu capture of 60 launches "
                                        "(profiles/apply_traffic_exciton7_r20_fp64.md)",
-                     "peak_source": "nominal FP64 (recipe table; not in MEASURED_PEAKS.json)",
+                     "peak_source": "FP64 torch.matmul 4096^3 measured in this run (peaks.fp64_tflops); "
+                                    "nominal FP64 is %.2f" % FP64_PEAK_TFLOPS,
+                     "kernel_time": "share of the device time of the replayed step graph (CUDA events recorded "
+                                    "as graph nodes, ttn_profile 2) x ms_per_step of the timed run",
+                     "kernel_ms_per_step": t_dom / args.steps,
+                     "frac_of_nominal_fp64": achieved / FP64_PEAK_TFLOPS,
                      "launches_per_step": n_l / args.steps},
-        "node_contraction": {"tflops_kernel": (k1_flops / (k1_ms * 1e-3) / 1e12) if k1_ms > 0 else None,
+        "node_contraction": {"tflops_kernel": (k1_flops / args.steps) / (share[0] * (ms_max / args.steps) * 1e-3) / 1e12
+                             if share[0] > 0 else None,
                              "tflops_step": flops[0] / (ms_max * 1e-3) / 1e12,
                              "gflop_per_step": flops[0] / args.steps / 1e9,
-                             "share_of_step_time": k1_ms / (ms_max if ms_max > 0 else 1)},
-        "kernel_time_share": {names[k]: prof[k][2] / sum(p[2] for p in prof.values()) for k in range(4)},
+                             "share_of_step_time": share[0]},
+        "kernel_time_share": {names[k]: share[k] for k in range(4)},
+        "kernel_ms_per_step": {names[k]: share[k] * ms_max / args.steps for k in range(4)},
+        "kernel_event_ms_sum_over_step": prof_sum / ms_prof if ms_prof > 0 else None,
         "plain_fp64_steps_per_s": value,
         "mixed_fp32": {"steps_per_s": world * args.steps / (ms_mixed * 1e-3),
                        "speedup_vs_plain_fp64": ms_max / ms_mixed,
@@ -472,6 +637,9 @@ def bench_ours(args, rank, world, local_rank):
                 "includes": "handle build, sop_load, workspace bind, rho0 upload, K steps with rho_S read back each step"},
         "batched": batch_out,
         "precision_rank64": r64,
+        "config1_spin_boson_tt": c1,
+        "ps2_learned_rank": p2,
+        "peaks": peaks,
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "wall_s_timed_region": wall,
@@ -489,6 +657,12 @@ def bench_ours(args, rank, world, local_rank):
         out["cpu_baseline"] = {"value": n_o / orc["seconds"], "unit": "steps/s", "cores": 1, "kind": "oracle",
                                "sample": f"first {n_o} ps1 steps of the same workload (numpy FP64, 1 thread)",
                                "cpu": cpu_model()}
+        ncpu = os.cpu_count() or 1
+        orc_all = run_oracle(budget_s=args.cpu_budget, max_steps=args.steps + args.warmup, threads=ncpu)
+        out["cpu_baseline_all_cores"] = {
+            "value": orc_all["steps"] / orc_all["seconds"], "unit": "steps/s", "cores": ncpu, "kind": "oracle",
+            "sample": f"first {orc_all['steps']} ps1 steps (numpy FP64 oracle, BLAS/OpenMP threads = {ncpu}; "
+                      "the oracle's per-term products are small, so threads add little)", "cpu": cpu_model()}
         out["rdm_err_vs_oracle"] = {"max_abs": err, "steps_compared": n_o}
     print(json.dumps(out), flush=True)
 
@@ -522,6 +696,11 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-rank64", action="store_true", help="skip the rank-64 precision leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
+    ap.add_argument("--no-ps2", action="store_true", help="skip the adaptive-rank / learned-proposer leg")
+    ap.add_argument("--ps2-only", action="store_true", help="print only the adaptive-rank leg")
+    ap.add_argument("--ps2-steps", type=int, default=200)
+    ap.add_argument("--ps2-pade", type=int, default=5, help="Pade features of the adaptive-rank workload")
+    ap.add_argument("--ps2-cap", type=int, default=32)
     ap.add_argument("--rank64-only", choices=["fp64", "mixed"], default=None,
                     help="profiling aid: run only the rank-64 leg in one form (prints that object, not the bench line)")
     ap.add_argument("--batch", type=int, default=256, help="instances in the batched leg")
