@@ -202,6 +202,8 @@ def rank64_leg(args, pkg, torch, flush, local_rank, forms=(("fp64", 0), ("mixed_
     rhos = {}
     for label, prec in forms:
         gg = make_gpu(pkg, w64, local_rank, precision=prec)
+        if prec == pkg.TTN_MIXED_FP32 and args.tensor_cores is not None:
+            gg.ttn_set_params(tensor_cores=args.tensor_cores)
         if not args.no_autotune:
             gg.ttn_autotune(2)
         gg.ttn_step(w64.dt, 1, 1)  # warm-up (graph capture)
@@ -697,6 +699,8 @@ def main():
     ap.add_argument("--no-rank64", action="store_true", help="skip the rank-64 precision leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--no-ps2", action="store_true", help="skip the adaptive-rank / learned-proposer leg")
+    ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
+                    help="tensor-core form of the rank-64 mixed leg (library default 1, thread-staged)")
     ap.add_argument("--ps2-only", action="store_true", help="print only the adaptive-rank leg")
     ap.add_argument("--ps2-steps", type=int, default=200)
     ap.add_argument("--ps2-pade", type=int, default=5, help="Pade features of the adaptive-rank workload")

@@ -100,6 +100,13 @@ typedef struct {
  *                    (contracted legs <= 64, >= 16384 elements) on the
  *                    tcgen05 tensor cores in 3xTF32 (hi/lo split, FP32
  *                    accumulation); 0 keeps them on the FP32 CUDA cores.
+ *                    1 stages the tensor operand by the threads, chunk by
+ *                    chunk; 2 splits the tensor operands into tf32 hi / lo
+ *                    tiles first and streams both operands by bulk copies
+ *                    through a 4-stage ring (one producer thread, one MMA
+ *                    thread). Both give the same results bit for bit; on the
+ *                    rank-64 chain the ring kernel is ~15 % faster per launch
+ *                    but its split pass costs as much as it saves.
  *  wait_s    (2.0)   0..60: upper bound, in seconds, of every device-side wait
  *                    of the kernels whose blocks wait on one another (the grid
  *                    barriers of the Jacobi SVD); a wait that runs out is
@@ -221,7 +228,9 @@ ttn_status ttn_batch_step(ttn_t* hs, int32_t n, double dt, int32_t scheme, int32
  * stage update), 1 = environment update (mode products + projection),
  * 2 = Householder QR, 3 = everything else (absorb, copies, RDM, drive, checks).
  * ttn_stats: launches and algorithmic FLOPs issued since the last reset
- * (complex multiply-add = 8 FLOPs), counted on the host, always on.
+ * (complex multiply-add = 8 FLOPs), counted on the host, always on. Kind 4
+ * (launches only) counts the job lists issued on the tensor-core ring path
+ * (tensor_cores = 2), at issue time: a captured step graph counts once.
  * ttn_profile(h, 1) additionally brackets every launch with CUDA events on the
  * handle's stream (the step is then issued launch by launch, not as a graph);
  * ttn_profile(h, 2) keeps the captured step graph and records the bracketing

@@ -53,6 +53,8 @@ struct ttn_ctx {
   double2* qr_work = nullptr;
   int64_t qr_elems = 0;
   float2* tc_acc = nullptr;  // FP32 scratch of the tensor-core path (mixed form)
+  float* tc_bsplit = nullptr;  // pre-split tensor operands of the tensor-core ring kernel
+  int64_t tc_bsplit_floats = 0;
   int64_t tc_acc_elems = 0;  // its capacity: three node-sized leg planes
   // pre-split operator matrices of the tensor-core path: on when some job list
   // was tensor-core eligible at bind time; every writer of those matrices
@@ -91,6 +93,7 @@ struct ttn_ctx {
 
   // kernel accounting (ttn_stats / ttn_profile)
   int64_t n_launch[4] = {0, 0, 0, 0};
+  int64_t n_ring = 0;  // job lists issued on the tensor-core ring path (counted at issue, ttn_stats kind 4)
   double n_flops[4] = {0, 0, 0, 0};
   bool profiling = false;  // per-launch events (mode 1) or event nodes in the step graph (mode 2)
   int prof_mode = 0;
@@ -205,7 +208,8 @@ ttn_status cuda_fail(ttn_t h, cudaError_t e, const char* what) {
 // ---------------------------------------------------------------------------
 struct Layout {
   size_t nodes, pool, scratch, qr, rdm, rho, bufs_tab, mats_tab, terms, outs, pjs, drives, flag, total;
-  size_t nodes32 = 0, pool32 = 0, scratch32 = 0, bufs_tab_lo = 0, mats_tab_lo = 0, tc_acc = 0;  // FP32 mode only
+  size_t nodes32 = 0, pool32 = 0, scratch32 = 0, bufs_tab_lo = 0, mats_tab_lo = 0, tc_acc = 0, tc_bsplit = 0;
+  int64_t tc_bsplit_floats = 0;  // FP32 mode only
   size_t tc_pool = 0, tc_off = 0;
   std::vector<int64_t> tc_off_host;  // float offset of each matrix in tc_pool, -1 if none
   size_t svd_small = 0, rsvd = 0, mlp = 0;
@@ -287,6 +291,13 @@ Layout layout_of(const Plan& p, int prec) {
     }
     L.tc_pool = take(std::max<int64_t>(pf, 1) * sizeof(float));
     L.tc_off = take(p.mats.size() * sizeof(int64_t));
+    // pre-split tensor operands of the ring kernel: the largest need of a
+    // tensor-core list (the lists run one after another on the stream)
+    for (const ApList& al : p.ap_lists)
+      if (al.n_tiles > 0 && tc_applicable(al, p.ap_outs.data(), p.ap_terms.data()))
+        L.tc_bsplit_floats =
+            std::max(L.tc_bsplit_floats, tc_split_floats(al, p.ap_outs.data(), p.ap_terms.data(), L.tc_off_host.data()));
+    L.tc_bsplit = take(std::max<int64_t>(L.tc_bsplit_floats, 1) * sizeof(float));
     L.mats_tab_lo = take(p.mats.size() * sizeof(void*));
   }
   L.total = off;
@@ -332,9 +343,14 @@ struct Exec {
     if (h->prec == PREC_F32 && h->params.tensor_cores && h->tc_acc &&
         tc_applicable(L, p.ap_outs.data(), p.ap_terms.data())) {
       run(kind, L.flops, [&] {
+        const bool ring = h->params.tensor_cores == 2;  // 1: thread-staged tensor operand
+        bool used_ring = false;
         if (!launch_apply_tc(h->Tlo, L, e, p.ap_outs.data(), p.ap_terms.data(), h->tc_acc, h->tc_acc_elems, h->flag_dev,
-                             h->tc_pool_on ? h->tc_pool : nullptr, h->tc_pool_on ? h->tc_off_dev : nullptr, s))
+                             h->tc_pool_on ? h->tc_pool : nullptr, h->tc_pool_on ? h->tc_off_dev : nullptr, s,
+                             h->tc_off.data(), ring ? h->tc_bsplit : nullptr, ring ? h->tc_bsplit_floats : 0,
+                             &used_ring))
           launch_apply(h->prec, h->Tlo, L, e, s);
+        if (used_ring) ++h->n_ring;
       });
       return;
     }
@@ -881,7 +897,7 @@ ttn_status ttn_set_params(ttn_t h, const ttn_params* prm) {
     if (!prm) return h->fail(TTN_EINVAL, "null params");
     if (!(prm->qr_tol >= 0) || !(prm->kappa > 0) || !(prm->ps2_atol >= 0) || !(prm->ps2_ratio >= 1) ||
         prm->max_rank < 1 || !(prm->svd_tol >= 0) || prm->max_split < 1 || prm->max_split > kMaxSplit ||
-        (prm->tensor_cores != 0 && prm->tensor_cores != 1) || !(prm->wait_s >= 0.0 && prm->wait_s <= 60.0))
+        (prm->tensor_cores < 0 || prm->tensor_cores > 2) || !(prm->wait_s >= 0.0 && prm->wait_s <= 60.0))
       return h->fail(TTN_EINVAL, "parameter out of range");
     if (h->ws_bound && prm->max_rank != h->params.max_rank)
       return h->fail(TTN_ESTATE, "max_rank must be set before the workspace is bound");
@@ -1077,6 +1093,8 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
       h->tc_pool = (float*)(base + L.tc_pool);
       h->tc_off_dev = (int64_t*)(base + L.tc_off);
       h->tc_off = L.tc_off_host;
+      h->tc_bsplit = (float*)(base + L.tc_bsplit);
+      h->tc_bsplit_floats = L.tc_bsplit_floats;
       h->tc_pool_on = false;
       for (const ApList& al : p.ap_lists)
         h->tc_pool_on = h->tc_pool_on || (al.n_tiles > 0 && tc_applicable(al, p.ap_outs.data(), p.ap_terms.data()));
@@ -1397,7 +1415,12 @@ ttn_status ttn_batch_step(ttn_t* hs, int32_t n, double dt, int32_t scheme, int32
 }
 
 ttn_status ttn_stats(ttn_t h, int32_t kind, int64_t* launches, double* flops) {
-  if (!h || kind < 0 || kind > 3) return TTN_EINVAL;
+  if (!h || kind < 0 || kind > 4) return TTN_EINVAL;
+  if (kind == 4) {
+    if (launches) *launches = h->n_ring;
+    if (flops) *flops = 0.0;
+    return TTN_OK;
+  }
   if (launches) *launches = h->n_launch[kind];
   if (flops) *flops = h->n_flops[kind];
   return TTN_OK;
@@ -1509,6 +1532,7 @@ ttn_status ttn_autotune(ttn_t h, int32_t reps) {
 ttn_status ttn_stats_reset(ttn_t h) {
   if (!h) return TTN_EINVAL;
   CUDA_TRY(h, h->drain_marks());
+  h->n_ring = 0;
   for (int k = 0; k < 4; ++k) {
     h->n_launch[k] = 0;
     h->n_flops[k] = 0;

@@ -61,9 +61,19 @@ void launch_apply(int prec, const DevTables& T, const ApList& L, const Epi& e, c
 // pool/pool_off (nullable): pre-split operator matrices (launch_tc_embed),
 // pool_off[mat] the float offset of a matrix or -1 (staged by the threads).
 bool tc_applicable(const ApList& L, const ApOut* outs_host, const ApTerm* terms_host);
+// pool_off_host: host copy of pool_off. bsplit (nullable, bsplit_floats floats):
+// buffer of the pre-split tensor operands; when every term of the list has a
+// pre-split operator and the list's split operands fit (tc_split_floats), the
+// tensor operands are split there first (k_tc_split) and both operands stream
+// into a 4-stage ring by bulk copies (k_tc_apply_ring); otherwise the threads
+// stage the tensor operand (k_tc_apply).
 bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const ApOut* outs_host,
                      const ApTerm* terms_host, float2* acc, int64_t acc_elems, int* flag, const float* pool,
-                     const int64_t* pool_off, cudaStream_t s);
+                     const int64_t* pool_off, cudaStream_t s, const int64_t* pool_off_host = nullptr,
+                     float* bsplit = nullptr, int64_t bsplit_floats = 0, bool* used_ring = nullptr);
+// Floats of pre-split tensor operands a list needs on the ring path (0: not eligible).
+int64_t tc_split_floats(const ApList& L, const ApOut* outs_host, const ApTerm* terms_host,
+                        const int64_t* pool_off_host);
 // Pre-split copies of FP32 operator matrices for the tensor-core path: for
 // each job, matrix `mat` (d x d, d <= 64) of the FP32 matrix table is embedded
 // and split into tf32 hi / lo in the layout the apply kernel stages, at float

@@ -606,12 +606,399 @@ __global__ void k_tc_epilogue(DevTables T, ApList L, Epi ep, const float2* acc, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pre-split tensor operand and the bulk-copy ring.
+//
+// k_tc_split writes, for one (source tensor, contracted leg) pair, the B
+// operand of every (64-position tile, 32-float K chunk) block exactly as the
+// staging above lays it out in shared memory: hi then lo, each kTcN x kTcK
+// floats in the canonical K-major layout, one contiguous 16 KB block per
+// (tile, chunk). k_tc_apply_ring then moves both operands of a chunk with two
+// bulk asynchronous copies (32 KB of operator, 16 KB of tensor) into a ring
+// of kRing stages: one producer thread issues the copies (completing on the
+// stage's `full` mbarrier), one MMA thread waits for `full`, issues the 12
+// MMAs of the chunk and commits them to the stage's `empty` mbarrier, which
+// the producer waits on before it refills the stage. No CTA barrier runs in
+// the chunk loop; the other warps join for the epilogue only.
+// ---------------------------------------------------------------------------
+constexpr int kRing = 4;
+constexpr size_t kRingSmem = (size_t)kRing * kStageFloats * sizeof(float);  // 192 KB
+constexpr int kTcMaxSplitJobs = 96;
+struct TcSplitJob {
+  int32_t src, leg, d0, d1, d2, tiles, nkc, pad;
+  int64_t off;  // float offset of the pair's blocks in the split buffer
+};
+struct TcSplitJobs {
+  int n;
+  int start[kTcMaxSplitJobs + 1];  // first block of each job (prefix sums of tiles * nkc)
+  TcSplitJob job[kTcMaxSplitJobs];
+};
+constexpr int kTcMaxListTerms = 320;
+struct TcBOff {
+  int t0, n;                       // terms t0 .. t0 + n - 1 of the global table
+  int64_t off[kTcMaxListTerms];    // float offset of each term's split tensor operand (-1: none)
+};
+
+__global__ void __launch_bounds__(kTcThreads) k_tc_split(DevTables T, TcSplitJobs J, float* __restrict__ bs) {
+  const int b = blockIdx.x;
+  if (b >= J.start[J.n]) return;
+  int j = 0;
+  while (j + 1 < J.n && J.start[j + 1] <= b) ++j;
+  const TcSplitJob jb = J.job[j];
+  const int local = b - J.start[j];
+  const int tile = local / jb.nkc, kc = local % jb.nkc;
+  const float2* __restrict__ X = (const float2*)T.bufs[jb.src];
+  const int d[3] = {jb.d0, jb.d1, jb.d2};
+  const int64_t st[3] = {(int64_t)jb.d1 * jb.d2, jb.d2, 1};
+  const int l = jb.leg, la = l == 0 ? 1 : 0, lb = l == 2 ? 1 : 2;
+  const int dl = d[l];
+  const int64_t rest = (int64_t)jb.d0 * jb.d1 * jb.d2 / dl;
+  float* Bh = bs + jb.off + ((int64_t)tile * jb.nkc + kc) * 2 * kBElems;
+  float* Bl = Bh + kBElems;
+  const int x0 = kc * (kTcK / 2);
+#pragma unroll
+  for (int q = 0; q < kBp; ++q) {
+    int nn, xp;
+    b_item(threadIdx.x + q * kTcThreads, l == 2, nn, xp);
+    const int64_t n = (int64_t)tile * kTcN + nn;
+    const int x = x0 + 2 * xp;
+    float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    if (n < rest) {
+      const int64_t base = (n / d[lb]) * st[la] + (n % d[lb]) * st[lb];
+      if (x < dl) a = X[(int64_t)x * st[l] + base];
+      if (x + 1 < dl) c = X[(int64_t)(x + 1) * st[l] + base];
+    }
+    const int o = cm_off(nn, 4 * xp);
+    const float4 h = make_float4(tf32_hi(a.x), tf32_hi(a.y), tf32_hi(c.x), tf32_hi(c.y));
+    *reinterpret_cast<float4*>(Bh + o) = h;
+    *reinterpret_cast<float4*>(Bl + o) =
+        make_float4(tf32_hi(a.x - h.x), tf32_hi(a.y - h.y), tf32_hi(c.x - h.z), tf32_hi(c.y - h.w));
+  }
+}
+
+__device__ __forceinline__ void bulk_g2s(float* dst, const float* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Same CTA -> (output, leg, tile, term part) mapping and outputs as
+// k_tc_apply; every term needs its operator in the pool and its tensor
+// operand in the split buffer (the host checks both).
+__global__ void __launch_bounds__(kTcThreads) k_tc_apply_ring(DevTables T, ApList L, int leg, TcLegs lg, float2* part,
+                                                             int64_t pstride, int* flag, const float* pool,
+                                                             const int64_t* pool_off, const float* bsplit,
+                                                             TcBOff boff) {
+  extern __shared__ __align__(128) float tsm[];
+  __shared__ __align__(8) uint64_t full[kRing], empty[kRing], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int64_t base[kTcN];
+  __shared__ int s_terms[kTcMaxTerms];
+  __shared__ int s_o, s_tile, s_n, s_earlier;
+  __shared__ ApTerm s_all[kTcMaxTerms];
+  __shared__ int64_t s_poff[kTcMaxTerms], s_boff[kTcMaxTerms];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool planes = leg < 0;
+  int o = L.out_begin, tile = blockIdx.x;
+  int split = 0, nsplit = 1;
+  if (planes) {
+    const int bx = (int)blockIdx.x;
+    leg = bx >= lg.lt[2] ? 2 : bx >= lg.lt[1] ? 1 : 0;
+    nsplit = lg.ks[leg];
+    const int ntile = (lg.lt[leg + 1] - lg.lt[leg]) / nsplit;
+    split = (bx - lg.lt[leg]) / ntile;
+    tile = (bx - lg.lt[leg]) % ntile;
+  } else {
+    if (warp == 0) {
+      int found = -1, left = tile;
+      for (int o0 = L.out_begin; o0 < L.out_end && found < 0; o0 += 32) {
+        int nt = 0;
+        if (o0 + lane < L.out_end) {
+          const ApOut u = T.outs[o0 + lane];
+          const int dl = leg == 0 ? u.d0 : leg == 1 ? u.d1 : u.d2;
+          nt = (int)(((int64_t)u.d0 * u.d1 * u.d2 / dl + kTcN - 1) / kTcN);
+        }
+        int inc = nt;
+        for (int k = 1; k < 32; k <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, inc, k);
+          if (lane >= k) inc += v;
+        }
+        const unsigned hit = __ballot_sync(0xffffffffu, left < inc);
+        if (hit) {
+          const int fl = __ffs(hit) - 1;
+          found = o0 + fl;
+          left -= __shfl_sync(0xffffffffu, inc - nt, fl);
+        } else {
+          left -= __shfl_sync(0xffffffffu, inc, 31);
+        }
+      }
+      if (lane == 0) {
+        s_o = found;
+        s_tile = left;
+      }
+    }
+    __syncthreads();
+    if (s_o < 0) return;
+    o = s_o;
+    tile = s_tile;
+  }
+  const ApOut out = T.outs[o];
+  const Geo3 g = geo_of(out);
+  const int64_t rest = (int64_t)out.d0 * out.d1 * out.d2 / g.d[leg];
+  const int n_all = out.term_end - out.term_begin;  // <= kTcMaxTerms (host check)
+  if (tid < n_all) s_all[tid] = T.terms[out.term_begin + tid];
+  __syncthreads();
+  if (tid == 0) {
+    int n = 0, e = 0;
+    for (int t = 0; t < n_all; ++t) {
+      const ApTerm tm = s_all[t];
+      if (tm.mat < 0) continue;
+      if (tm.leg == leg) s_terms[n++] = out.term_begin + t;
+      if (tm.leg < leg) e = 1;
+    }
+    s_n = n;
+    s_earlier = e;
+  }
+  __syncthreads();
+  const int n_here = s_n;
+  const bool earlier = planes ? false : s_earlier != 0;
+  if (tid < n_here) {
+    const int t = s_terms[tid];
+    s_poff[tid] = pool_off[T.terms[t].mat];
+    s_boff[tid] = boff.off[t - boff.t0];
+  }
+  if (n_here == 0) return;  // uniform
+  const int d = g.d[leg];
+  const int nkc = (2 * d + kTcK - 1) / kTcK;
+  const int k_begin = split * n_here / nsplit;
+  const int n_mine = (split + 1) * n_here / nsplit - k_begin;
+  const int nchunks = n_mine * nkc;
+  const int64_t n0 = (int64_t)tile * kTcN;
+  const int nvalid = rest - n0 < kTcN ? (int)(rest - n0) : kTcN;
+  {
+    const int la = leg == 0 ? 1 : 0, lb = leg == 2 ? 1 : 2;
+    for (int nn = tid; nn < kTcN; nn += kTcThreads) {
+      const int64_t n = n0 + nn;
+      base[nn] = (n / g.d[lb]) * g.st[la] + (n % g.d[lb]) * g.st[lb];
+    }
+  }
+  float2* Y = part ? part + (planes ? (int64_t)(lg.pb[leg] + split) * pstride : 0) : (float2*)T.bufs[out.dst];
+  if (tid == 0) {
+    for (int s = 0; s < kRing; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+  const uint64_t deadline = gtimer() + 1000000000ull;
+  bool ok = true;
+  // producer: thread 0; issued[s] = copies into stage s so far (the k-th
+  // completes phase k - 1 of full[s]). MMA thread: warp 1 lane 0.
+  int issued[kRing] = {0, 0, 0, 0};
+  bool mma_pending = false;  // MMAs issued (the drain commits and waits for them)
+  // lanes 1..31 of the two role warps park at __syncwarp (no spinning next
+  // to their lane 0); the other warps wait for `done` below
+  if (tid == 0) {
+    for (int ci = 0; ci < nchunks && ok; ++ci) {
+      const int s = ci % kRing;
+      if (ci >= kRing) ok = mbar_wait(&empty[s], (uint32_t)(((ci / kRing) - 1) & 1), deadline);
+      if (!ok) break;
+      const int k = k_begin + ci / nkc, kc = ci % nkc;
+      float* buf = tsm + s * kStageFloats;
+      const uint32_t abytes = 2u * kAElems * 4u, bbytes = 2u * kBElems * 4u;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
+                   "r"(abytes + bbytes)
+                   : "memory");
+      bulk_g2s(buf, pool + s_poff[k] + (int64_t)kc * 2 * kAElems, abytes, &full[s]);
+      bulk_g2s(buf + 2 * kAElems, bsplit + s_boff[k] + ((int64_t)tile * nkc + kc) * 2 * kBElems, bbytes, &full[s]);
+      ++issued[s];
+    }
+  } else if (tid == 32) {
+    for (int ci = 0; ci < nchunks && ok; ++ci) {
+      const int s = ci % kRing;
+      ok = mbar_wait(&full[s], (uint32_t)((ci / kRing) & 1), deadline);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ah = smem_u32(tsm + s * kStageFloats), al = ah + kAElems * 4, bh = al + kAElems * 4,
+                     bl = bh + kBElems * 4;
+      const uint32_t a_op[3] = {ah, ah, al}, b_op[3] = {bh, bl, bh};
+#pragma unroll
+      for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+        for (int ks = 0; ks < kTcK / 8; ++ks) {
+          const uint64_t ad = sdesc(a_op[pass] + ks * 256), bd = sdesc(b_op[pass] + ks * 256);
+          const uint32_t accum = (ci > 0 || pass > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+              : "memory");
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&empty[s]))
+                   : "memory");
+      mma_pending = true;
+    }
+    if (ok) {
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&done))
+                   : "memory");
+    }
+  }
+  if (warp < 2) __syncwarp();
+  // every thread: the accumulator is complete once `done` has fired
+  if (ok) ok = mbar_wait(&done, 0u, deadline);
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok) {
+    if (tid == 0) atomicOr(flag, 8);
+    // drain: no copy may still land in shared memory and no MMA may still run
+    // once the CTA frees its tensor memory and exits
+    const uint64_t drain = gtimer() + 1000000000ull;
+    if (tid == 0)
+      for (int s = 0; s < kRing; ++s)
+        if (issued[s] > 0) mbar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1), drain);
+    if (tid == 32 && mma_pending) {
+      // a commit tracks every MMA this thread issued before it
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&done))
+                   : "memory");
+      mbar_wait(&done, 0u, drain);
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  float* Ds = tsm;  // [128][65], the ring is idle now
+  if (ok) {
+    const int q = warp & 3, h = warp >> 2;
+    uint32_t r[32];
+    const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int row = 32 * q + lane;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) Ds[row * 65 + 32 * h + j] = __uint_as_float(r[j]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+  if (!ok) return;
+  for (int e = tid; e < d * kTcN; e += kTcThreads) {
+    const int i = e / kTcN, nn = e % kTcN;
+    if (nn >= nvalid) continue;
+    const int64_t at = (int64_t)i * g.st[leg] + base[nn];
+    float2 v = make_float2(Ds[(2 * i) * 65 + nn], Ds[(2 * i + 1) * 65 + nn]);
+    if (earlier) {
+      const float2 y = Y[at];
+      v.x += y.x;
+      v.y += y.y;
+    }
+    Y[at] = v;
+  }
+}
+
+// Split plan of a list for the ring kernel: the distinct (source, leg) pairs of
+// its tensor-core terms, their blocks in the split buffer, and every term's
+// offset. False when the list does not fit the kernel's tables (more than
+// kTcMaxTerms terms on an output, kTcMaxListTerms in the list, kTcMaxSplitJobs
+// pairs) or some operator has no pre-split copy (pool_off_host < 0).
+bool tc_ring_plan(const ApList& L, const ApOut* outs, const ApTerm* terms, const int64_t* pool_off_host,
+                  TcSplitJobs* J, TcBOff* B, int64_t* floats) {
+  int t0 = 1 << 30, t1 = 0;
+  for (int o = L.out_begin; o < L.out_end; ++o) {
+    const ApOut& u = outs[o];
+    if (u.term_end - u.term_begin > kTcMaxTerms) return false;
+    t0 = std::min(t0, u.term_begin);
+    t1 = std::max(t1, u.term_end);
+  }
+  if (t1 <= t0 || t1 - t0 > kTcMaxListTerms) return false;
+  B->t0 = t0;
+  B->n = t1 - t0;
+  for (int i = 0; i < kTcMaxListTerms; ++i) B->off[i] = -1;
+  J->n = 0;
+  int64_t off = 0;
+  for (int o = L.out_begin; o < L.out_end; ++o) {
+    const ApOut& u = outs[o];
+    const int dd[3] = {u.d0, u.d1, u.d2};
+    const int64_t P = (int64_t)u.d0 * u.d1 * u.d2;
+    for (int t = u.term_begin; t < u.term_end; ++t) {
+      const ApTerm& tm = terms[t];
+      if (tm.mat < 0) continue;
+      if (!pool_off_host || pool_off_host[tm.mat] < 0) return false;
+      int j = 0;
+      for (; j < J->n; ++j) {
+        const TcSplitJob& q = J->job[j];
+        if (q.src == tm.src && q.leg == tm.leg && q.d0 == u.d0 && q.d1 == u.d1 && q.d2 == u.d2) break;
+      }
+      if (j == J->n) {
+        if (J->n == kTcMaxSplitJobs) return false;
+        TcSplitJob q{};
+        q.src = tm.src;
+        q.leg = tm.leg;
+        q.d0 = u.d0;
+        q.d1 = u.d1;
+        q.d2 = u.d2;
+        q.tiles = (int)((P / dd[tm.leg] + kTcN - 1) / kTcN);
+        q.nkc = (2 * dd[tm.leg] + kTcK - 1) / kTcK;
+        q.off = off;
+        off += (int64_t)q.tiles * q.nkc * 2 * kBElems;
+        J->job[J->n++] = q;
+      }
+      B->off[t - t0] = J->job[j].off;
+    }
+  }
+  J->start[0] = 0;
+  for (int j = 0; j < J->n; ++j) J->start[j + 1] = J->start[j] + J->job[j].tiles * J->job[j].nkc;
+  *floats = off;
+  return true;
+}
+
 }  // namespace
+
+int64_t tc_split_floats(const ApList& L, const ApOut* outs_host, const ApTerm* terms_host,
+                        const int64_t* pool_off_host) {
+  thread_local TcSplitJobs J;
+  thread_local TcBOff B;
+  int64_t f = 0;
+  return tc_ring_plan(L, outs_host, terms_host, pool_off_host, &J, &B, &f) ? f : 0;
+}
 
 bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const ApOut* outs_host,
                      const ApTerm* terms_host, float2* acc, int64_t acc_elems, int* flag, const float* pool,
-                     const int64_t* pool_off, cudaStream_t s) {
+                     const int64_t* pool_off, cudaStream_t s, const int64_t* pool_off_host, float* bsplit,
+                     int64_t bsplit_floats, bool* used_ring) {
+  if (used_ring) *used_ring = false;
   if (L.n_tiles <= 0) return true;
+  // the bulk-copy ring when both operands of every term can arrive pre-split
+  thread_local TcSplitJobs J;  // kernel arguments (copied at launch); per thread: handles are independent
+  thread_local TcBOff B;
+  int64_t need = 0;
+  const bool ring = pool && pool_off && bsplit &&
+                    tc_ring_plan(L, outs_host, terms_host, pool_off_host, &J, &B, &need) && need <= bsplit_floats;
+  static bool ring_attr = false;
+  if (ring && !ring_attr) {
+    cudaFuncSetAttribute(k_tc_apply_ring, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmem);
+    ring_attr = true;
+  }
+  if (ring && J.start[J.n] > 0) k_tc_split<<<J.start[J.n], kTcThreads, 0, s>>>(T, J, bsplit);
+  if (used_ring) *used_ring = ring;
   const bool rk = e.mode != EPI_STORE;
   const bool one = L.out_end - L.out_begin == 1;
   if (rk && (!one || !acc)) return false;
@@ -685,7 +1072,13 @@ bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const Ap
       lg.lt[l + 1] = lg.lt[l] + n;
       if (has[l]) q += lg.ks[l];
     }
-    if (lg.lt[3] > 0) k_tc_apply<<<lg.lt[3], kTcThreads, kTcSmem, s>>>(T, L, -1, lg, acc, P, flag, pool, pool_off);
+    if (lg.lt[3] > 0) {
+      if (ring)
+        k_tc_apply_ring<<<lg.lt[3], kTcThreads, kRingSmem, s>>>(T, L, -1, lg, acc, P, flag, pool, pool_off, bsplit,
+                                                                B);
+      else
+        k_tc_apply<<<lg.lt[3], kTcThreads, kTcSmem, s>>>(T, L, -1, lg, acc, P, flag, pool, pool_off);
+    }
     k_tc_epilogue<<<L.n_tiles, 32, 0, s>>>(T, L, e, acc, q, P);
     return true;
   }
@@ -693,7 +1086,11 @@ bool launch_apply_tc(const DevTables& T, const ApList& L, const Epi& e, const Ap
   for (int l = 0; l < 3; ++l)
     if (has[l]) {
       float2* part = rk ? acc : nullptr;  // RK lists: the single output's sum goes to acc
-      k_tc_apply<<<tiles[l], kTcThreads, kTcSmem, s>>>(T, L, l, none, part, 0, flag, pool, pool_off);
+      if (ring)
+        k_tc_apply_ring<<<tiles[l], kTcThreads, kRingSmem, s>>>(T, L, l, none, part, 0, flag, pool, pool_off, bsplit,
+                                                                B);
+      else
+        k_tc_apply<<<tiles[l], kTcThreads, kTcSmem, s>>>(T, L, l, none, part, 0, flag, pool, pool_off);
     }
   if (rk || ident) k_tc_epilogue<<<L.n_tiles, 32, 0, s>>>(T, L, e, acc, 0, 0);
   return true;

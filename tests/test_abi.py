@@ -88,7 +88,7 @@ def test_params_round_trip_and_range_checks(lib):
     assert lib.ttn_get_params(h, C.byref(p)) == 0
     assert (p.qr_tol, p.kappa, p.max_rank, p.max_split, p.tensor_cores) == (1e-9, 2.5, 32, 8, 1)
     for field, bad in (("max_split", 0), ("max_split", 9), ("kappa", 0.0), ("ps2_ratio", 0.5), ("max_rank", 0),
-                       ("tensor_cores", 2)):
+                       ("tensor_cores", 3), ("tensor_cores", -1), ("wait_s", -1.0), ("wait_s", 61.0)):
         q = _lib.ttn_params()
         C.memmove(C.byref(q), C.byref(p), C.sizeof(p))
         setattr(q, field, bad)

@@ -86,22 +86,35 @@ def test_rank64_seven_site_chain_mixed_vs_fp64(pkg):
 
 def test_rank64_tensor_cores_match_cuda_cores(pkg):
     """The mixed form with its large mode products on the tcgen05 tensor cores
-    (3xTF32) against the same form on the FP32 CUDA cores and the oracle."""
+    (3xTF32) against the same form on the FP32 CUDA cores and the oracle. The
+    bulk-copy ring (pre-split tensor operand, tensor_cores = 2) and the
+    thread-staged kernel (tensor_cores = 1) feed the MMAs the same operands in
+    the same order, so their results are identical bit for bit."""
     w = W.exciton_chain(n_sites=3, depth=4, rank=64)
     ga = gpu_from(pkg, w, precision=pkg.TTN_MIXED_FP32)
+    ga.ttn_set_params(tensor_cores=2)
+    gs = gpu_from(pkg, w, precision=pkg.TTN_MIXED_FP32)
     gb = gpu_from(pkg, w, precision=pkg.TTN_MIXED_FP32)
     gb.ttn_set_params(tensor_cores=0)
+    for g in (ga, gs, gb):  # the environment build at bind ran with the default form
+        g.ttn_stats_reset()
     o = ottn.from_workload(w)
     e_tc = e_ref = diff = 0.0
     for _ in range(3):
         ga.ttn_step(w.dt, pkg.TTN_PS1, 1)
+        gs.ttn_step(w.dt, pkg.TTN_PS1, 1)
         gb.ttn_step(w.dt, pkg.TTN_PS1, 1)
         o.step(w.dt, "ps1")
-        ra, rb, ro = ga.ttn_rdm(), gb.ttn_rdm(), o.rdm()
+        ra, rs, rb, ro = ga.ttn_rdm(), gs.ttn_rdm(), gb.ttn_rdm(), o.rdm()
+        assert np.array_equal(ra, rs)
         e_tc = max(e_tc, float(np.max(np.abs(ra - ro))))
         e_ref = max(e_ref, float(np.max(np.abs(rb - ro))))
         diff = max(diff, float(np.max(np.abs(ra - rb))))
+    for u in range(len(w.parent)):
+        assert np.array_equal(ga.ttn_get_node(u), gs.ttn_get_node(u)), u
+    assert ga.ttn_stats(4)[0] > 0 and gs.ttn_stats(4)[0] == 0  # the ring path ran (and only where asked)
     ga.close()
+    gs.close()
     gb.close()
     assert e_tc <= 1e-6 and e_ref <= 1e-6
     assert diff <= 1e-6
