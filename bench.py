@@ -407,6 +407,67 @@ def ps2_leg(args, pkg, torch, local_rank) -> dict:
             "leg_seconds": time.perf_counter() - leg_t0}
 
 
+def paper_models_leg(pkg, torch, local_rank, flush, sweeps: bool) -> dict:
+    """The paper's example models (Sec. 3.2 Table 1, Sec. 3.4, Sec. 3.2.3 Table 2)
+    on the GPU: steps/s of the structured spin-boson (1000 fs) and of the
+    three-site FMO model with six Brownian peaks at 77 K (45 features), and --
+    with `sweeps` -- the convergence study of Table 2: the time-averaged
+    |rho_11 - rho_11^ref| over 1000 fs for hierarchy depths (panel a, BTT,
+    reference depth 25) and bond ranks (panels b / c, BTT and TT, reference
+    rank 40)."""
+    def timed(w, steps, precision=0):
+        g = make_gpu(pkg, w, local_rank, precision=precision)
+        g.ttn_step(w.dt, 1, 2)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(g.stream):
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(g.stream)
+        g.ttn_step(w.dt, 1, steps)
+        b.record(g.stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        rho = g.ttn_rdm()
+        g.close()
+        return steps / (ms * 1e-3), rho
+
+    def traj(w, steps):
+        g = make_gpu(pkg, w, local_rank)
+        out = []
+        for _ in range(steps):
+            g.ttn_step(w.dt, 1, 1)
+            out.append(g.ttn_rdm()[1, 1].real)  # rho_11 of the paper = the second state's population
+        g.close()
+        return np.array(out)
+
+    res = {}
+    w = W.structured_spin_boson()
+    sps, rho = timed(w, 1000)
+    res["structured_spin_boson"] = {"workload": w.name + ", dt 1 fs, 1000 steps, ps1 FP64", "steps_per_s": sps,
+                                    "rho_11_at_1000_fs": float(rho[1, 1].real)}
+    w = W.fmo3(T=77.0)
+    s64, r64 = timed(w, 200)
+    s32, r32 = timed(w, 200, precision=pkg.TTN_MIXED_FP32)
+    res["fmo3_77K_bo6"] = {"workload": w.name + ", dt 0.05 fs, 200 steps after 2 warm-up steps, ps1",
+                           "steps_per_s_fp64": s64, "steps_per_s_mixed": s32,
+                           "rdm_max_abs_mixed_vs_fp64": float(np.max(np.abs(r64 - r32))),
+                           "populations_fp64": [float(r64[i, i].real) for i in range(3)]}
+    if sweeps:
+        n = 1000
+        ref_a = traj(W.convergence_spin_boson("a", depth=25, rank=40), n)
+        res["table2_depth_sweep_btt"] = {
+            str(d): float(np.mean(np.abs(traj(W.convergence_spin_boson("a", depth=d, rank=40), n) - ref_a)))
+            for d in (2, 4, 6, 10, 14)}
+        for tree in ("btt", "tt"):
+            ref = traj(W.convergence_spin_boson("b", depth=25, rank=40, tree=tree), n)
+            res[f"table2_rank_sweep_{tree}"] = {
+                str(r): float(np.mean(np.abs(traj(W.convergence_spin_boson("b", depth=25, rank=r, tree=tree), n) - ref)))
+                for r in (2, 4, 8, 12, 16, 24, 32)}
+        res["table2_note"] = ("mean over 1000 steps (1 fs) of |rho_11 - rho_11(reference)|; reference depth 25 "
+                              "(panel a) and rank 40 (panels b, c) of the same tree")
+    return res
+
+
 def bench_ours(args, rank, world, local_rank):
     import torch
     import paper_2603_17711_gb300 as pkg
@@ -420,6 +481,10 @@ def bench_ours(args, rank, world, local_rank):
     if args.accuracy_steps:  # long trajectory: mixed against FP64 on the GPU, step by step
         if rank == 0:
             print(json.dumps({"accuracy": accuracy_leg(args, pkg, torch, w, local_rank)}), flush=True)
+        return
+    if args.paper_only:  # the paper's example models with the Table 2 convergence sweeps
+        if rank == 0:
+            print(json.dumps({"paper_models": paper_models_leg(pkg, torch, local_rank, flush, True)}), flush=True)
         return
     if args.ps2_only:  # only the adaptive-rank leg
         if rank == 0:
@@ -499,6 +564,8 @@ def bench_ours(args, rank, world, local_rank):
     r64 = None if args.no_rank64 else rank64_leg(args, pkg, torch, flush, local_rank)
     # ---- the spin-boson tensor train, 1000 steps against the stored oracle trajectory ----
     c1 = config1_leg(pkg, torch, local_rank, flush)
+    # ---- the paper's example models (throughput; the sweeps run with --paper-only) ----
+    pm = paper_models_leg(pkg, torch, local_rank, flush, False)
     # ---- adaptive rank: SVD rule against the learned rank proposer ----
     p2 = None if args.no_ps2 else ps2_leg(args, pkg, torch, local_rank)
 
@@ -641,6 +708,7 @@ def bench_ours(args, rank, world, local_rank):
         "precision_rank64": r64,
         "config1_spin_boson_tt": c1,
         "ps2_learned_rank": p2,
+        "paper_models": pm,
         "peaks": peaks,
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -702,6 +770,8 @@ def main():
     ap.add_argument("--tensor-cores", type=int, default=None, choices=[0, 1, 2],
                     help="tensor-core form of the rank-64 mixed leg (library default 1, thread-staged)")
     ap.add_argument("--ps2-only", action="store_true", help="print only the adaptive-rank leg")
+    ap.add_argument("--paper-only", action="store_true",
+                    help="print only the paper's example models, with the Table 2 convergence sweeps")
     ap.add_argument("--ps2-steps", type=int, default=200)
     ap.add_argument("--ps2-pade", type=int, default=5, help="Pade features of the adaptive-rank workload")
     ap.add_argument("--ps2-cap", type=int, default=32)

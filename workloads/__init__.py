@@ -268,3 +268,106 @@ def random_density_matrix(rng: np.random.Generator, M: int) -> np.ndarray:
     A = rng.normal(size=(M, M)) + 1j * rng.normal(size=(M, M))
     rho = A @ A.conj().T
     return rho / np.trace(rho).real
+
+
+# ----------------------------------------------------------------------------
+# The paper's own example models (Sec. 3): parameters as printed there
+# ----------------------------------------------------------------------------
+
+def _kelvin_beta(T: float) -> float:
+    """1 / (k_B T) in fs (energies in rad/fs)."""
+    return 1.0 / (KB_CM1_PER_K * T * CM1_TO_RAD_PER_FS)
+
+
+def structured_spin_boson(depth: int = 25, rank: int = 20, tree: str = "btt", n_steps: int = 1000,
+                          dt: float = 1.0, T: float = 300.0, n_ltc: int = 1) -> Workload:
+    """Example 1 (Sec. 3.2, Table 1 and the listing beside it): spin-boson
+    H_S = (1500/2) sz + 300 sx cm^-1 written as diag(-750, 750) + 300 sx (the
+    listing's matrix), coupling sys_op = diag(-1/2, 1/2), one bath with a
+    Drude-Lorentz term (lambda 540, omega_c 70 cm^-1) and one Brownian peak
+    (lambda 161.6, eta 10, omega_0' 1243 cm^-1) at 300 K, Pade with one
+    low-temperature correction (K = 1 + 2 + 1 = 4 features), depth 25,
+    dt 1 fs, 1000 fs, rho0 = |1><1| (second state, wfn = (0, 1)). The listing
+    leaves the tree, the rank and the propagator at TENSO's defaults; here: a
+    balanced binary tree, fixed rank (ps1)."""
+    c = CM1_TO_RAD_PER_FS
+    H = np.array([[-750.0, 300.0], [300.0, 750.0]], np.complex128) * c
+    bath = Bath(Q=np.diag([-0.5, 0.5]).astype(np.complex128), beta=_kelvin_beta(T), dl=(540.0 * c, 70.0 * c),
+                bo=[(161.6 * c, 1243.0 * c, 10.0 * c)], n_ltc=n_ltc)
+    K = bath.n_features
+    parent, leg_node = tensor_train(K) if tree == "tt" else balanced_binary(K)
+    rho0 = np.zeros((2, 2), np.complex128)
+    rho0[1, 1] = 1.0
+    return Workload(name=f"structured spin-boson (Table 1) {tree.upper()} K={K} N={depth} R={rank}", H=H,
+                    baths=[bath], depth=[depth] * K, parent=parent, leg_node=leg_node,
+                    ranks=uniform_ranks(parent, rank), rho0=rho0, dt=dt, n_steps=n_steps)
+
+
+FMO3_H_CM1 = np.array([[200.0, -87.7, 5.5], [-87.7, 320.0, 30.8], [5.5, 30.8, 0.0]])
+# six Brownian peaks of the structured FMO spectral density: (lambda, omega_0', eta) in cm^-1
+FMO_BO6_CM1 = [(26.24, 160.0, 133.0), (13.832, 247.0, 53.0), (101.479, 763.0, 76.0),
+               (57.575, 1175.0, 29.0), (25.764, 1356.0, 29.0), (9.126, 1521.0, 15.0)]
+
+
+def fmo3(T: float = 77.0, spectral: str = "bo6", depth: int = 20, rank: int = 16, n_steps: int = 20000,
+         dt: float = 0.05, n_ltc: Optional[int] = None) -> Workload:
+    """Example 2 (Sec. 3.4 and its listing): the three-site FMO model
+    (site Hamiltonian in cm^-1 as printed), an identical independent bath on
+    every site coupled through |i><i|, rho0 = |1><1|, dt 0.05 fs, 1000 fs,
+    depth 20, ps1. spectral: 'bo6' (six Brownian peaks), 'bo3' (the three
+    below 1000 cm^-1) or 'dl' (Drude-Lorentz 35 / 106.18 cm^-1); Pade with
+    n_ltc = 1 at 300 K and 3 at 77 K (the paper's choice). bo6 at 77 K gives
+    K = 12 + 3 = 15 features per site, 45 in all. Balanced binary tree; the
+    listing leaves the rank at TENSO's default, here `rank`."""
+    c = CM1_TO_RAD_PER_FS
+    if n_ltc is None:
+        n_ltc = 3 if T < 150.0 else 1
+    if spectral == "bo6":
+        bo, dl = [(l * c, w * c, e * c) for (l, w, e) in FMO_BO6_CM1], None
+    elif spectral == "bo3":
+        bo, dl = [(l * c, w * c, e * c) for (l, w, e) in FMO_BO6_CM1 if w < 1000.0], None
+    elif spectral == "dl":
+        bo, dl = [], (35.0 * c, 106.18 * c)
+    else:
+        raise ValueError(spectral)
+    baths = []
+    for i in range(3):
+        Q = np.zeros((3, 3), np.complex128)
+        Q[i, i] = 1.0
+        baths.append(Bath(Q=Q, beta=_kelvin_beta(T), dl=dl, bo=list(bo), n_ltc=n_ltc))
+    K = sum(b.n_features for b in baths)
+    parent, leg_node = balanced_binary(K)
+    rho0 = np.zeros((3, 3), np.complex128)
+    rho0[0, 0] = 1.0
+    return Workload(name=f"FMO 3-site {spectral} {T:g} K BTT K={K} N={depth} R={rank}",
+                    H=FMO3_H_CM1.astype(np.complex128) * c, baths=baths, depth=[depth] * K, parent=parent,
+                    leg_node=leg_node, ranks=uniform_ranks(parent, rank), rho0=rho0, dt=dt, n_steps=n_steps)
+
+
+def convergence_spin_boson(panel: str = "b", depth: int = 25, rank: int = 40, tree: str = "btt",
+                           n_steps: int = 1000, dt: float = 1.0, T: float = 300.0, n_ltc: int = 1) -> Workload:
+    """The spin-boson models of the convergence study (Sec. 3.2.3, Table 2):
+    panel 'a' -- symmetric (Delta eps = 0, V = 300 cm^-1), Drude-Lorentz bath
+    only (540, 70 cm^-1), coupled through sigma_x (the depth sweep);
+    panel 'b' -- Delta eps = 1500, V = 300, Drude-Lorentz (540, 70) plus a
+    Brownian peak (lambda 330, eta 4, omega_0' 1663), coupled through sigma_z
+    (the rank sweeps, BTT and TT). Temperature, Pade correction, dt and the
+    initial state follow the Example 1 listing (300 K, n_ltc 1, 1 fs,
+    rho0 = |1><1|)."""
+    c = CM1_TO_RAD_PER_FS
+    if panel == "a":
+        H = 300.0 * SIGMA_X * c
+        bath = Bath(Q=SIGMA_X.copy(), beta=_kelvin_beta(T), dl=(540.0 * c, 70.0 * c), n_ltc=n_ltc)
+    elif panel == "b":
+        H = (np.array([[-750.0, 0.0], [0.0, 750.0]]) + 300.0 * SIGMA_X.real).astype(np.complex128) * c
+        bath = Bath(Q=SIGMA_Z.copy(), beta=_kelvin_beta(T), dl=(540.0 * c, 70.0 * c),
+                    bo=[(330.0 * c, 1663.0 * c, 4.0 * c)], n_ltc=n_ltc)
+    else:
+        raise ValueError(panel)
+    K = bath.n_features
+    parent, leg_node = tensor_train(K) if tree == "tt" else balanced_binary(K)
+    rho0 = np.zeros((2, 2), np.complex128)
+    rho0[1, 1] = 1.0
+    return Workload(name=f"convergence spin-boson panel {panel} {tree.upper()} K={K} N={depth} R={rank}",
+                    H=H, baths=[bath], depth=[depth] * K, parent=parent, leg_node=leg_node,
+                    ranks=uniform_ranks(parent, rank), rho0=rho0, dt=dt, n_steps=n_steps)
