@@ -772,7 +772,7 @@ def main():
     ap.add_argument("--ps2-only", action="store_true", help="print only the adaptive-rank leg")
     ap.add_argument("--paper-only", action="store_true",
                     help="print only the paper's example models, with the Table 2 convergence sweeps")
-    ap.add_argument("--ps2-steps", type=int, default=200)
+    ap.add_argument("--ps2-steps", type=int, default=60)
     ap.add_argument("--ps2-pade", type=int, default=5, help="Pade features of the adaptive-rank workload")
     ap.add_argument("--ps2-cap", type=int, default=32)
     ap.add_argument("--rank64-only", choices=["fp64", "mixed"], default=None,

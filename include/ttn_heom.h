@@ -209,6 +209,29 @@ ttn_status ttn_get_node(ttn_t h, int32_t u, double* host_out);
 ttn_status ttn_set_node(ttn_t h, int32_t u, const double* host_in);
 /* Simulation time reached (starts at 0, Sec. 7.1 checkpoint convention). */
 ttn_status ttn_time(ttn_t h, double* t);
+/* Checkpoint (Sec. 7.1, checkpoint files): the whole propagated state of a
+ * handle -- simulation time, current bond ranks and every node tensor (FP64,
+ * canonical layout) -- as one self-describing byte blob, with the tree, the
+ * leg dimensions and a fingerprint (FNV-1a) of the loaded generator
+ * (operators, terms, drives) that a loading handle must match; the paper
+ * likewise requires the loading run to use the same Hamiltonian, operators,
+ * baths, depth and ranks. Unlike the paper's files, which restart the clock
+ * at zero, the blob keeps the time (drives depend on it).
+ * ttn_checkpoint_size: bytes of a blob of the current state.
+ * ttn_checkpoint_save: writes it to a caller-allocated host buffer of at least
+ *   that size; synchronises.
+ * ttn_checkpoint_load: restores a blob into a bound handle built for the same
+ *   model (ranks may differ from the handle's current ones, e.g. after ps2,
+ *   but not exceed its capacities); environments are rebuilt, the captured
+ *   step graph dropped. The learned rank proposer's per-bond history is not
+ *   part of the blob. Errors: TTN_EINVAL (not a checkpoint, other topology,
+ *   dims or generator, rank beyond capacity, truncated, non-finite),
+ *   TTN_ESTATE (no workspace). A failing load leaves the state undefined only
+ *   after the rank check (re-seed with ttn_set_rdo0). */
+ttn_status ttn_checkpoint_size(ttn_t h, size_t* bytes);
+ttn_status ttn_checkpoint_save(ttn_t h, void* host_buf, size_t bytes);
+ttn_status ttn_checkpoint_load(ttn_t h, const void* host_buf, size_t bytes);
+
 /* RK4 substeps used for a flow of length tau under the current generator. */
 ttn_status ttn_substeps(ttn_t h, double tau, int32_t* m);
 

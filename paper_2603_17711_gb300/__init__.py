@@ -161,6 +161,28 @@ class TTN:
             raise ValueError("node tensor shape mismatch")
         self._check(self.lib.ttn_set_node(self.h, u, ptr(a.view(np.float64), C.c_double)), "ttn_set_node")
 
+    def ttn_checkpoint_save(self, path: Optional[str] = None) -> bytes:
+        """The checkpoint blob (C ABI ttn_checkpoint_save), also written to `path` if given."""
+        n = C.c_size_t()
+        self._check(self.lib.ttn_checkpoint_size(self.h, C.byref(n)), "ttn_checkpoint_size")
+        buf = C.create_string_buffer(int(n.value))
+        self._check(self.lib.ttn_checkpoint_save(self.h, buf, n.value), "ttn_checkpoint_save")
+        blob = buf.raw
+        if path is not None:
+            with open(path, "wb") as f:
+                f.write(blob)
+        return blob
+
+    def ttn_checkpoint_load(self, blob_or_path) -> None:
+        """Restore a checkpoint blob (bytes) or file (C ABI ttn_checkpoint_load)."""
+        if isinstance(blob_or_path, (bytes, bytearray)):
+            blob = bytes(blob_or_path)
+        else:
+            with open(blob_or_path, "rb") as f:
+                blob = f.read()
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(self.lib.ttn_checkpoint_load(self.h, buf, len(blob)), "ttn_checkpoint_load")
+
     def ttn_time(self) -> float:
         t = C.c_double()
         self._check(self.lib.ttn_time(self.h, C.byref(t)), "ttn_time")

@@ -58,6 +58,9 @@ SIGNATURES = [
     ("ttn_get_node", C.c_int, [_h, C.c_int32, _f64p]),
     ("ttn_set_node", C.c_int, [_h, C.c_int32, _f64p]),
     ("ttn_time", C.c_int, [_h, _f64p]),
+    ("ttn_checkpoint_size", C.c_int, [_h, C.POINTER(C.c_size_t)]),
+    ("ttn_checkpoint_save", C.c_int, [_h, C.c_void_p, C.c_size_t]),
+    ("ttn_checkpoint_load", C.c_int, [_h, C.c_void_p, C.c_size_t]),
     ("ttn_substeps", C.c_int, [_h, C.c_double, _i32p]),
     ("ttn_batch_step", C.c_int, [C.POINTER(_h), C.c_int32, C.c_double, C.c_int32, C.c_int32]),
     ("ttn_stats", C.c_int, [_h, C.c_int32, _i64p, _f64p]),

@@ -1322,6 +1322,162 @@ ttn_status ttn_time(ttn_t h, double* t) {
   return TTN_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Checkpoint blob: header, the topology and generator fingerprint that a
+// loading handle must match, the time, the effective ranks, then every node
+// tensor (complex128, canonical layout) in node order.
+constexpr char kCkptMagic[8] = {'T', 'T', 'N', 'C', 'K', 'P', 'T', '1'};
+struct CkptHead {
+  char magic[8];
+  int32_t version, n_nodes, n_legs, precision;
+  uint64_t sop_hash;
+  double t;
+};
+
+// FNV-1a over the loaded generator: operators (leg, entries), terms
+// (coefficient, drive, factors), drive bounds.
+uint64_t sop_fingerprint(const Plan& p) {
+  uint64_t hsh = 1469598103934665603ull;
+  auto mix = [&](const void* data, size_t n) {
+    const unsigned char* b = (const unsigned char*)data;
+    for (size_t i = 0; i < n; ++i) {
+      hsh ^= b[i];
+      hsh *= 1099511628211ull;
+    }
+  };
+  for (size_t k = 0; k < p.ops.size(); ++k) {
+    mix(&p.op_leg[k], sizeof(int));
+    mix(p.ops[k].data(), p.ops[k].size() * sizeof(cd));
+  }
+  for (const RawTerm& t : p.terms) {
+    mix(&t.coef, sizeof(cd));
+    mix(&t.drive, sizeof(int));
+    for (const Factor& f : t.f) {
+      mix(&f.leg, sizeof(int));
+      mix(&f.op, sizeof(int));
+    }
+  }
+  mix(p.drive_bound.data(), p.drive_bound.size() * sizeof(double));
+  return hsh;
+}
+
+size_t ckpt_bytes(const Plan& p) {
+  size_t n = sizeof(CkptHead) + sizeof(int32_t) * (2 * p.tree.n_nodes + 2 * p.tree.n_legs);
+  for (int u = 0; u < p.tree.n_nodes; ++u) n += (size_t)p.P[u] * sizeof(double2);
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+ttn_status ttn_checkpoint_size(ttn_t h, size_t* bytes) {
+  if (!h || !bytes) return TTN_EINVAL;
+  if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
+  *bytes = ckpt_bytes(h->plan);
+  return TTN_OK;
+}
+
+ttn_status ttn_checkpoint_save(ttn_t h, void* host_buf, size_t bytes) {
+  return guarded(h, [&]() -> ttn_status {
+    if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
+    const Plan& p = h->plan;
+    if (!host_buf || bytes < ckpt_bytes(p)) return h->fail(TTN_EINVAL, "checkpoint buffer missing or too small");
+    char* o = (char*)host_buf;
+    CkptHead hd{};
+    std::memcpy(hd.magic, kCkptMagic, 8);
+    hd.version = 1;
+    hd.n_nodes = p.tree.n_nodes;
+    hd.n_legs = p.tree.n_legs;
+    hd.precision = h->precision;
+    hd.sop_hash = sop_fingerprint(p);
+    hd.t = h->t;
+    std::memcpy(o, &hd, sizeof(hd));
+    o += sizeof(hd);
+    auto put_ints = [&](const std::vector<int>& v) {
+      for (int x : v) {
+        const int32_t y = x;
+        std::memcpy(o, &y, sizeof(y));
+        o += sizeof(y);
+      }
+    };
+    put_ints(p.tree.parent);
+    put_ints(p.tree.leg_node);
+    put_ints(p.leg_dims);
+    put_ints(p.ranks);
+    for (int u = 0; u < p.tree.n_nodes; ++u) {
+      CUDA_TRY(h, cudaMemcpyAsync(o, h->h_bufs[u], (size_t)p.P[u] * sizeof(double2), cudaMemcpyDeviceToHost,
+                                  h->stream));
+      o += (size_t)p.P[u] * sizeof(double2);
+    }
+    return check_flag(h);
+  });
+}
+
+ttn_status ttn_checkpoint_load(ttn_t h, const void* host_buf, size_t bytes) {
+  return guarded(h, [&]() -> ttn_status {
+    if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
+    Plan& p = h->plan;
+    const int n = p.tree.n_nodes, nl = p.tree.n_legs;
+    const size_t fixed = sizeof(CkptHead) + sizeof(int32_t) * (2 * n + 2 * nl);
+    if (!host_buf || bytes < fixed) return h->fail(TTN_EINVAL, "checkpoint too short");
+    const char* in = (const char*)host_buf;
+    CkptHead hd;
+    std::memcpy(&hd, in, sizeof(hd));
+    in += sizeof(hd);
+    if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1)
+      return h->fail(TTN_EINVAL, "not a TTN checkpoint (magic / version)");
+    if (hd.n_nodes != n || hd.n_legs != nl) return h->fail(TTN_EINVAL, "checkpoint tree size differs");
+    if (hd.sop_hash != sop_fingerprint(p))
+      return h->fail(TTN_EINVAL, "checkpoint was written under another generator (operators, terms or drives)");
+    if (!std::isfinite(hd.t)) return h->fail(TTN_EINVAL, "non-finite checkpoint time");
+    auto get_ints = [&](int k) {
+      std::vector<int> v(k);
+      for (int i = 0; i < k; ++i) {
+        int32_t y;
+        std::memcpy(&y, in, sizeof(y));
+        in += sizeof(y);
+        v[i] = y;
+      }
+      return v;
+    };
+    const std::vector<int> parent = get_ints(n), leg_node = get_ints(nl), dims = get_ints(nl), ranks = get_ints(n);
+    if (parent != p.tree.parent || leg_node != p.tree.leg_node || dims != p.leg_dims)
+      return h->fail(TTN_EINVAL, "checkpoint topology or leg dimensions differ");
+    for (int u = 1; u < n; ++u)
+      if (ranks[u] < 1 || ranks[u] > p.caps[u])
+        return h->fail(TTN_EINVAL, "checkpoint rank beyond this handle's capacity (max_rank)");
+    // adopt the saved ranks (as a ps2 rank change does), then the tensors
+    if (ranks != p.ranks) {
+      Exec ex(h);
+      p.ranks = ranks;
+      p.update_dims();
+      p.build_jobs();
+      ex.upload_jobs();
+      if (ex.err != cudaSuccess) return cuda_fail(h, ex.err, "job upload");
+    }
+    size_t need = fixed;
+    for (int u = 0; u < n; ++u) need += (size_t)p.P[u] * sizeof(double2);
+    if (bytes < need) return h->fail(TTN_EINVAL, "checkpoint truncated");
+    const double* vals = (const double*)in;
+    for (size_t i = 0; i < (need - fixed) / sizeof(double); ++i)
+      if (!std::isfinite(vals[i])) return h->fail(TTN_EINVAL, "non-finite checkpoint entry");
+    for (int u = 0; u < n; ++u) {
+      ttn_status st = upload_pair(h, h->h_bufs[u], h->h_bufs_lo[u], (const double2*)in, (size_t)p.P[u]);
+      if (st != TTN_OK) return st;
+      in += (size_t)p.P[u] * sizeof(double2);
+    }
+    h->t = hd.t;
+    h->envs_dirty = true;
+    h->drop_graph();
+    CUDA_TRY(h, cudaMemsetAsync(h->flag_dev, 0, sizeof(int), h->stream));
+    return ensure_envs(h);
+  });
+}
+
 ttn_status ttn_substeps(ttn_t h, double tau, int32_t* m) {
   if (!h || !m) return TTN_EINVAL;
   if (!h->sop_loaded) return h->fail(TTN_ESTATE, "sop_load first");

@@ -47,8 +47,10 @@ def test_paper_models_against_oracle(pkg, make, n):
 def test_fmo_77k_full_size_both_forms(pkg):
     """45 features (six Brownian peaks and three Pade corrections per site),
     depth 20, rank 16, balanced binary tree: FP64 and mixed stay within the
-    1e-6 bar of each other over 40 steps (2 fs), the trace stays 1 and the
-    populations move away from site 1."""
+    1e-6 bar of each other over 40 steps (2 fs) and the populations move away
+    from site 1. At a truncated rank the trace is not conserved exactly (the
+    projected generator need not keep the n = 0 tier's trace); it is only
+    checked to stay near 1."""
     w = W.fmo3(T=77.0)
     ga = pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0)
     gb = pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0,
@@ -59,7 +61,7 @@ def test_fmo_77k_full_size_both_forms(pkg):
         gb.ttn_step(w.dt, pkg.TTN_PS1, 1)
         ra, rb = ga.ttn_rdm(), gb.ttn_rdm()
         diff = max(diff, float(np.max(np.abs(ra - rb))))
-    assert abs(np.trace(ra) - 1.0) < 1e-8
+    assert abs(np.trace(ra) - 1.0) < 1e-4
     assert ra[0, 0].real < 1.0 - 1e-4
     ga.close()
     gb.close()
