@@ -31,6 +31,12 @@ Plain numpy complex128 restatement of the TTN-HEOM hot path (Sec. 2.3):
 * ps2 (adaptive rank, Sec. 2.3 last paragraph and Sec. 7.5): neighbouring cores
   are merged, the pair is propagated, and an SVD splits it back with a
   truncated rank.
+* vmf (direct integration, Sec. 2.3 and Sec. 7.5): every node is advanced at
+  once by the projected equations of motion in the multilayer-MCTDH form
+  (non-root nodes kept semi-unitary, the root carries the weight; the inverse
+  of each single-hole density matrix regularised by vmf_atol on its diagonal),
+  integrated by dopri5 with the ode_rtol / ode_atol controller. 'mix' runs ps2
+  until a bond reaches max_rank, then vmf at the ranks ps2 reached.
 * Sub-flows use classical RK4 with m = max(1, ceil(|tau| Lambda / 2.5)) substeps,
   Lambda the static operator-norm bound of oracle.sop.lambda_bound.
 * Gauge moves use the Householder QR of ``householder_qr`` (diag(R) real >= 0;
@@ -40,7 +46,11 @@ Plain numpy complex128 restatement of the TTN-HEOM hot path (Sec. 2.3):
 
 Pinned by tests/test_oracle_ttn.py: untruncated ranks against the dense
 hierarchy, pure dephasing at rank >= M^2 against the closed form, TT against
-BTT, metric independence, QR against LAPACK, RK4 order.
+BTT, metric independence, QR against LAPACK, RK4 order; by
+tests/test_oracle_vmf.py: dopri5 against expm (fifth order), vmf at untruncated
+ranks against the dense hierarchy, vmf exact on the pure-dephasing manifold,
+the regularisation, the mixed strategy's switch; by tests/test_oracle_ps2_rule.py:
+the ps2 truncation rule and the SVD completion.
 """
 from __future__ import annotations
 
@@ -225,6 +235,66 @@ def rk4(apply, y: np.ndarray, tau: float, m: int) -> np.ndarray:
     return y
 
 
+# Dormand-Prince 5(4) tableau (Dormand & Prince 1980; the FSAL form of
+# Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.5).
+DP_C = [0.0, 1 / 5, 3 / 10, 4 / 5, 8 / 9, 1.0, 1.0]
+DP_A = [[],
+        [1 / 5],
+        [3 / 40, 9 / 40],
+        [44 / 45, -56 / 15, 32 / 9],
+        [19372 / 6561, -25360 / 2187, 64448 / 6561, -212 / 729],
+        [9017 / 3168, -355 / 33, 46732 / 5247, 49 / 176, -5103 / 18656],
+        [35 / 384, 0.0, 500 / 1113, 125 / 192, -2187 / 6784, 11 / 84]]
+DP_B5 = [35 / 384, 0.0, 500 / 1113, 125 / 192, -2187 / 6784, 11 / 84, 0.0]
+DP_B4 = [5179 / 57600, 0.0, 7571 / 16695, 393 / 640, -92097 / 339200, 187 / 2100, 1 / 40]
+
+
+def dopri5(f, y0: List[np.ndarray], t0: float, t1: float, h_try: float, rtol: float, atol: float,
+           max_steps: int = 100000):
+    """Integrate dy/dt = f(t, y) from t0 to t1 (y a list of arrays) with the
+    Dormand-Prince 5(4) pair and the standard step controller. A step of
+    length h = min(h_try, t1 - t) has the scaled RMS error
+        err = sqrt(mean(|y5 - y4|^2 / (atol + rtol max(|y_n|, |y_n+1|))^2))
+    over all entries; it is accepted when err <= 1, and the trial step becomes
+    h * min(5, max(0.2, 0.9 err^(-1/5))) (a shortened step that lands on t1
+    does not shrink the trial step). Returns (y(t1), the trial step for the next
+    interval, accepted, rejected)."""
+    y = [np.array(a, np.complex128) for a in y0]
+    t = t0
+    acc = rej = 0
+    k1 = f(t, y)
+    n_steps = 0
+    while t1 - t > 1e-13 * max(1.0, abs(t1)):
+        n_steps += 1
+        if n_steps > max_steps:
+            raise RuntimeError("dopri5: too many steps")
+        last = h_try >= t1 - t
+        h = t1 - t if last else h_try
+        ks = [k1]
+        for i in range(1, 7):
+            yi = [y[j] + h * sum(DP_A[i][l] * ks[l][j] for l in range(i)) for j in range(len(y))]
+            ks.append(f(t + DP_C[i] * h, yi))
+        y5 = yi  # stage 7 is evaluated at the fifth-order solution (first same as last)
+        num, cnt = 0.0, 0
+        for j in range(len(y)):
+            e = h * sum((DP_B5[l] - DP_B4[l]) * ks[l][j] for l in range(7))
+            sc = atol + rtol * np.maximum(np.abs(y[j]), np.abs(y5[j]))
+            num += float(np.sum(np.abs(e / sc) ** 2))
+            cnt += e.size
+        err = float(np.sqrt(num / max(cnt, 1)))
+        fac = 5.0 if err == 0.0 else min(5.0, max(0.2, 0.9 * err ** (-0.2)))
+        if err <= 1.0:
+            t = t1 if last else t + h
+            y = y5
+            k1 = ks[6]
+            acc += 1
+            h_try = max(h_try, h * fac) if last else h * fac
+        else:
+            rej += 1
+            h_try = h * fac
+    return y, h_try, acc, rej
+
+
 def svd_completion(W: np.ndarray, s: np.ndarray, Vh: np.ndarray, tol: float):
     """Kept singular triplets with sigma_i <= tol * sigma_1 are numerically
     undetermined; replace them by a deterministic completion (sigma_i := 0, the
@@ -269,6 +339,12 @@ class Params:
     ps2_ratio: float = 2.0
     max_rank: int = 32
     svd_tol: float = 1e-12
+    # vmf (direct integration, Sec. 7.5): dopri5 tolerances (Sec. 4 Table
+    # defaults ode_rtol / ode_atol) and the regularisation vmf_atol added to
+    # the diagonal of the single-hole density matrix before its inversion
+    ode_rtol: float = 1e-5
+    ode_atol: float = 1e-7
+    vmf_atol: float = 1e-10
 
 
 class TTN:
@@ -542,11 +618,142 @@ class TTN:
         self.psi_adj(0, h, first=True)
         self.t = t0 + dt
 
+    # -- vmf: direct integration of the node equations (Sec. 2.3, Sec. 7.5) ----
+    def _upper(self, tensors):
+        """Weighted quantities of the part of the tree above every non-root
+        node u (all nodes but u's subtree, with the root's weight), from the
+        isometric environments of the subtrees below:
+          rho[u][a', a]   = <Psi_up[a'] | Psi_up[a]>
+          mf[u][m][a', a] = <Psi_up[a'] | h_m^up | Psi_up[a]>  (None: h_m has
+                            no factor above u, i.e. h_m^up = 1 and mf = rho)
+        computed top-down: the overlap and the mean field on an edge p -> u
+        contract conj(U_p), U_p over p's legs other than u, with the parent
+        edge's weighted quantity on p's parent leg, the children's bottom-up
+        environments on the sibling legs and the operators on open legs."""
+        rho: Dict[int, np.ndarray] = {}
+        mf: Dict[int, List[Optional[np.ndarray]]] = {}
+        for p in self.tree_preorder():
+            U = tensors[p]
+            legs = self.tree.legs[p]
+            for c in self.tree.children[p]:
+                lc = legs.index(("n", c))
+                other = [i for i in range(U.ndim) if i != lc]
+                # overlap: weight on the parent leg only
+                W = U
+                if p != 0:
+                    W = mode_product(rho[p], W, 0)
+                rho[c] = np.tensordot(U.conj(), W, axes=(other, other))
+                above = set(range(len(self.leg_dims))) - set(self.tree.below[c])
+                out: List[Optional[np.ndarray]] = []
+                for m, term in enumerate(self.terms):
+                    if not (set(term.ops) & above):
+                        out.append(None)
+                        continue
+                    W = U
+                    for li in other:
+                        kind, v = legs[li]
+                        if kind == "p":
+                            F = mf[p][m] if mf[p][m] is not None else rho[p]
+                        elif kind == "n":
+                            F = self.env[(v, p)][m]
+                        else:
+                            F = term.ops.get(v)
+                        if F is not None:
+                            W = mode_product(F, W, li)
+                    out.append(np.tensordot(U.conj(), W, axes=(other, other)))
+                mf[c] = out
+        return rho, mf
+
+    def tree_preorder(self) -> List[int]:
+        out: List[int] = []
+
+        def rec(u):
+            out.append(u)
+            for c in self.tree.children[u]:
+                rec(c)
+        rec(0)
+        return out
+
+    def vmf_rhs(self, tensors) -> List[np.ndarray]:
+        """Time derivative of every node tensor under the Dirac-Frenkel
+        projected generator with the gauge <U_u | dU_u/dt> = 0 (the standard
+        multilayer MCTDH equations, written for the linear generator L):
+          root:  dA/dt = sum_m coef_m (prod_l E_l(m) x_l) A
+          u:     dU_u/dt = rho_u,reg^-1 x_parent (1 - P_u) G_u,
+                 G_u = sum_m coef_m mf_u(m) x_parent (prod_child E_l(m) x_l) U_u,
+        with rho_reg = rho + vmf_atol * 1 (the regularisation of Sec. 7.5),
+        P_u the projector onto the span of U_u's rows (parent index fixed) and
+        mf_u(m) = rho_u when term m has no factor above u."""
+        saved = self.tensors
+        self.tensors = tensors
+        try:
+            for c in self.tree.postorder():  # isometric (bottom-up) environments
+                if c != 0:
+                    self.update_env(c, self.tree.parent[c])
+            rho, mf = self._upper(tensors)
+            out = [None] * self.tree.n_nodes
+            out[0] = self.apply_node(0, tensors[0])
+            for u in range(1, self.tree.n_nodes):
+                U = tensors[u]
+                G = np.zeros_like(U)
+                for m in range(len(self.terms)):
+                    W = U
+                    for li in range(1, U.ndim):
+                        E = self.leg_env(u, li, m)
+                        if E is not None:
+                            W = mode_product(E, W, li)
+                    F = mf[u][m] if mf[u][m] is not None else rho[u]
+                    G += self.coef(m) * mode_product(F, W, 0)
+                Um = U.reshape(U.shape[0], -1)
+                Gm = G.reshape(U.shape[0], -1)
+                Gm = Gm - (Gm @ Um.conj().T) @ Um
+                r = rho[u].shape[0]
+                Rinv = np.linalg.inv(rho[u] + self.params.vmf_atol * np.eye(r))
+                out[u] = (Rinv @ Gm).reshape(U.shape)
+            return out
+        finally:
+            self.tensors = saved
+
+    def step_vmf(self, dt: float) -> None:
+        """One step of length dt of the direct integration: all node tensors
+        advanced together by dopri5 (ode_rtol, ode_atol), the first trial step
+        dt and then the controller's trial step carried over from the previous
+        interval; drive values taken at the stage times. Environments are
+        refreshed at the end."""
+        p = self.params
+        t0 = self.t
+        h0 = getattr(self, "_vmf_h", dt)
+
+        def f(t, y):
+            self.g = [d.g(t) for d in self.drives]
+            return self.vmf_rhs(y)
+        y, h_next, acc, rej = dopri5(f, self.tensors, t0, t0 + dt, h0, p.ode_rtol, p.ode_atol)
+        self._vmf_h = h_next
+        self.vmf_stats = getattr(self, "vmf_stats", [0, 0])
+        self.vmf_stats[0] += acc
+        self.vmf_stats[1] += rej
+        self.tensors = y
+        self.t = t0 + dt
+        for c in self.tree.postorder():
+            if c != 0:
+                self.update_env(c, self.tree.parent[c])
+
     def step(self, dt: float, scheme: str = "ps1") -> None:
         if scheme == "ps1":
             self.step_ps1(dt)
         elif scheme == "ps2":
             self.step_ps2(dt)
+        elif scheme == "vmf":
+            self.step_vmf(dt)
+        elif scheme == "mix":
+            # the paper's default strategy (Sec. 3.2.3, Sec. 7.5): ps2 while the ranks
+            # adapt, then direct integration at the ranks ps2 reached; read here as:
+            # switch after the first ps2 step at which a bond rank reaches max_rank
+            if getattr(self, "_mixed_to_vmf", False):
+                self.step_vmf(dt)
+            else:
+                self.step_ps2(dt)
+                self._mixed_to_vmf = max(self.ranks[1:] or [0]) >= self.params.max_rank
         else:
             raise ValueError(scheme)
 
