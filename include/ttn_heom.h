@@ -61,9 +61,11 @@ typedef enum {
  * accumulation and the reduced density matrix are FP64 in every mode. */
 enum { TTN_FP64 = 0, TTN_MIXED_FP32 = 1 };
 
-/* Propagation schemes (Sec. 2.3): ps1 fixed rank, ps2 adaptive rank.
- * vmf (direct integration) is not implemented: TTN_EUNSUPPORTED. */
-enum { TTN_PS1 = 1, TTN_PS2 = 2, TTN_VMF = 3 };
+/* Propagation schemes (Sec. 2.3, Sec. 7.5): ps1 fixed rank, ps2 adaptive rank,
+ * vmf direct integration of all node equations at fixed rank (FP64 form),
+ * mix = ps2 until a bond rank reaches max_rank, vmf from then on (the
+ * paper's default strategy). */
+enum { TTN_PS1 = 1, TTN_PS2 = 2, TTN_VMF = 3, TTN_MIX = 4 };
 
 /* Tree topology: parent[0] = -1 (node 0 is the root), parent[u] in [0, n_nodes)
  * otherwise; leg_node[l] = node carrying open leg l. */
@@ -110,7 +112,11 @@ typedef struct {
  *  wait_s    (2.0)   0..60: upper bound, in seconds, of every device-side wait
  *                    of the kernels whose blocks wait on one another (the grid
  *                    barriers of the Jacobi SVD); a wait that runs out is
- *                    reported as TTN_ETIMEOUT (no counterpart in the paper). */
+ *                    reported as TTN_ETIMEOUT (no counterpart in the paper).
+ *  ode_rtol  (1e-5)  vmf: relative and absolute tolerance of the dopri5
+ *  ode_atol  (1e-7)  controller (Sec. 4, Table 4 defaults).
+ *  vmf_atol  (1e-10) vmf: added to the diagonal of every single-hole density
+ *                    matrix before it is inverted (Sec. 7.5 regularisation). */
 typedef struct {
   double qr_tol;
   double kappa;
@@ -121,6 +127,9 @@ typedef struct {
   int32_t max_split;
   int32_t tensor_cores;
   double wait_s;
+  double ode_rtol;
+  double ode_atol;
+  double vmf_atol;
 } ttn_params;
 
 /* Create a handle (Sec. 2.3, Eq. omega_tensor). leg_dims[n_legs]: leg
@@ -178,8 +187,17 @@ ttn_status ttn_set_stream(ttn_t h, void* stream);
  * rho0: M*M complex, row-major. Resets time to 0 and rebuilds environments. */
 ttn_status ttn_set_rdo0(ttn_t h, const double* rho0);
 
-/* Advance n_steps steps of length dt with scheme TTN_PS1 or TTN_PS2 (one step =
- * the symmetric composition of a half sweep over dt/2 and its adjoint). The
+/* Advance n_steps steps of length dt. TTN_PS1 / TTN_PS2: one step = the
+ * symmetric composition of a half sweep over dt/2 and its adjoint. TTN_VMF:
+ * every node tensor advanced together over dt by the Dormand-Prince 5(4) pair
+ * with adaptive substeps (ode_rtol, ode_atol; the trial step carried from one
+ * call to the next) under the multilayer-MCTDH node equations -- the root
+ * carries the weight, every other node stays semi-unitary (its derivative is
+ * projected off its own span) and is multiplied by the inverse of its
+ * regularised single-hole density matrix (vmf_atol); FP64 form only
+ * (TTN_EUNSUPPORTED in the mixed form); not captured as a graph (the step
+ * control synchronises). TTN_MIX: ps2 steps until a bond reaches max_rank,
+ * TTN_VMF steps at the reached ranks afterwards (reset by ttn_set_rdo0). The
  * orthogonality centre is at the root before and after. Asynchronous on the
  * handle's stream except for drive sampling on the host. For an autonomous
  * generator on a non-default stream the kernels of one ps1 step are captured

@@ -13,11 +13,11 @@ from typing import Callable, Optional, Sequence
 import numpy as np
 
 from . import heom
-from ._lib import (DRIVE_FN, TTN_FP64, TTN_MIXED_FP32, TTN_OK, TTN_PS1, TTN_PS2, TTN_VMF,
+from ._lib import (DRIVE_FN, TTN_FP64, TTN_MIXED_FP32, TTN_MIX, TTN_OK, TTN_PS1, TTN_PS2, TTN_VMF,
                    TTNError, as_f64, as_i32, ptr, ttn_params, ttn_tree)
 from . import _lib
 
-__all__ = ["TTN", "TTNError", "heom", "TTN_FP64", "TTN_MIXED_FP32", "TTN_PS1", "TTN_PS2", "TTN_VMF",
+__all__ = ["TTN", "TTNError", "heom", "TTN_FP64", "TTN_MIXED_FP32", "TTN_PS1", "TTN_PS2", "TTN_VMF", "TTN_MIX",
            "library", "from_model", "ttn_batch_step", "RankProposer"]
 
 _LIB: Optional[C.CDLL] = None

@@ -18,7 +18,7 @@ TTN_OK, TTN_EINVAL, TTN_ENOMEM, TTN_ECUDA, TTN_ENUMERIC, TTN_ETIMEOUT, TTN_ESTAT
 STATUS_NAMES = ["TTN_OK", "TTN_EINVAL", "TTN_ENOMEM", "TTN_ECUDA", "TTN_ENUMERIC", "TTN_ETIMEOUT",
                 "TTN_ESTATE", "TTN_EUNSUPPORTED"]
 TTN_FP64, TTN_MIXED_FP32 = 0, 1
-TTN_PS1, TTN_PS2, TTN_VMF = 1, 2, 3
+TTN_PS1, TTN_PS2, TTN_VMF, TTN_MIX = 1, 2, 3, 4
 
 
 class ttn_tree(C.Structure):
@@ -29,7 +29,8 @@ class ttn_tree(C.Structure):
 class ttn_params(C.Structure):
     _fields_ = [("qr_tol", C.c_double), ("kappa", C.c_double), ("ps2_atol", C.c_double),
                 ("ps2_ratio", C.c_double), ("max_rank", C.c_int32), ("svd_tol", C.c_double),
-                ("max_split", C.c_int32), ("tensor_cores", C.c_int32), ("wait_s", C.c_double)]
+                ("max_split", C.c_int32), ("tensor_cores", C.c_int32), ("wait_s", C.c_double),
+                ("ode_rtol", C.c_double), ("ode_atol", C.c_double), ("vmf_atol", C.c_double)]
 
 
 DRIVE_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libttnheom.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["plan.cpp", "kernels.cu", "qr.cu", "qr_blocked.cu", "tc_apply.cu", "ps2.cu", "svd.cu", "mlp.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["plan.cpp", "kernels.cu", "qr.cu", "qr_blocked.cu", "tc_apply.cu", "ps2.cu", "svd.cu", "vmf.cu", "mlp.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -32,7 +32,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct ttn_ctx {
   Plan plan;
   int precision = TTN_FP64;
-  ttn_params params{1e-9, 2.5, 1e-7, 2.0, 32, 1e-12, kMaxSplit, 1, 2.0};
+  ttn_params params{1e-9, 2.5, 1e-7, 2.0, 32, 1e-12, kMaxSplit, 1, 2.0, 1e-5, 1e-7, 1e-10};
   bool sop_loaded = false;
   bool ws_bound = false;
   bool envs_dirty = true;
@@ -69,6 +69,18 @@ struct ttn_ctx {
   int* svd_perm = nullptr;
   int* svd_info = nullptr;
   unsigned* svd_sync = nullptr;  // barrier counters of the grid Jacobi SVD
+  // direct integration (vmf), FP64 form only
+  double2 *vmf_y = nullptr, *vmf_save = nullptr, *vmf_tmp = nullptr, *vmf_r = nullptr, *vmf_aug = nullptr,
+          *vmf_dmi = nullptr, *vmf_x = nullptr, *vmf_ctmp = nullptr;
+  double2* vmf_k[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int* vmf_slots = nullptr;
+  double* vmf_err = nullptr;
+  int64_t vmf_n = 0;                 // complex elements of the flat node region
+  std::vector<int64_t> node_off, vmf_r_off;
+  std::vector<int> vmf_slot_off;
+  double vmf_h = 0.0;                // dopri5 trial step carried between calls
+  int64_t vmf_acc = 0, vmf_rej = 0;  // dopri5 steps accepted / rejected
+  bool mix_switched = false;         // TTN_MIX: ps2 phase over
   std::vector<double> discarded;  // discarded weight of every ps2 split (host log)
   std::vector<int> init_ranks;
   // learned rank proposer
@@ -213,6 +225,14 @@ struct Layout {
   size_t tc_pool = 0, tc_off = 0;
   std::vector<int64_t> tc_off_host;  // float offset of each matrix in tc_pool, -1 if none
   size_t svd_small = 0, rsvd = 0, mlp = 0;
+  // direct integration (vmf): committed state, per-node saves, 7 stage
+  // derivatives (all as flat copies of the node region), edge scratch
+  size_t vmf_y = 0, vmf_save = 0, vmf_k = 0, vmf_tmp = 0, vmf_r = 0, vmf_aug = 0, vmf_dmi = 0, vmf_x = 0,
+         vmf_ctmp = 0, vmf_slots = 0, vmf_err = 0;
+  int64_t nodes_elems = 0;
+  std::vector<int64_t> vmf_r_off;   // complex offset of each bond's R in vmf_r
+  std::vector<int> vmf_slot_off;    // offset of each directed edge's class slots in vmf_slots
+  std::vector<int> vmf_slot_host;   // the class slots themselves
   std::vector<int64_t> node_off;  // complex elements from `nodes`
   std::vector<int64_t> rdm_off;
   int64_t scratch_elems = 0, qr_elems = 0, rdm_elems = 0;
@@ -269,6 +289,35 @@ Layout layout_of(const Plan& p, int prec) {
   L.rsvd = take(3 * p.theta_cap * sizeof(double2));
   L.mlp = take((24 + 13 + mlp_ws_floats(1) + 8) * sizeof(float) + 2 * sizeof(double));
   L.flag = take(sizeof(int) * 4);
+  if (prec == PREC_F64) {
+    L.nodes_elems = acc;
+    L.vmf_y = take(acc * sizeof(double2));
+    L.vmf_save = take(acc * sizeof(double2));
+    L.vmf_k = take(7 * acc * sizeof(double2));
+    L.vmf_tmp = take(p.P_cap_max * sizeof(double2));
+    L.vmf_r_off.assign(n, 0);
+    int64_t ro = 0;
+    int max_cls = 0;
+    for (int c = 1; c < n; ++c) {
+      L.vmf_r_off[c] = ro;
+      ro += (int64_t)p.caps[c] * p.caps[c];
+    }
+    L.vmf_r = take(std::max<int64_t>(ro, 1) * sizeof(double2));
+    const int64_t r2 = (int64_t)p.r_cap_max * p.r_cap_max;
+    L.vmf_aug = take(3 * r2 * sizeof(double2));
+    L.vmf_dmi = take(r2 * sizeof(double2));
+    L.vmf_x = take(r2 * sizeof(double2));
+    L.vmf_slot_off.assign(2 * n + 1, 0);
+    for (int e = 0; e < 2 * n; ++e) {
+      L.vmf_slot_off[e] = (int)L.vmf_slot_host.size();
+      for (int sl : p.dir_slots[e]) L.vmf_slot_host.push_back(sl);
+      max_cls = std::max(max_cls, (int)p.dir_slots[e].size());
+    }
+    L.vmf_slot_off[2 * n] = (int)L.vmf_slot_host.size();
+    L.vmf_ctmp = take(std::max<int64_t>(2 * r2 * max_cls, 1) * sizeof(double2));
+    L.vmf_slots = take(std::max<size_t>(L.vmf_slot_host.size(), 1) * sizeof(int));
+    L.vmf_err = take(1025 * sizeof(double));
+  }
   if (prec == PREC_F32) {
     L.nodes32 = take(acc * sizeof(float2));
     L.pool32 = take(std::max<int64_t>(p.mat_pool, 1) * sizeof(float2));
@@ -717,6 +766,62 @@ struct Exec {
     psi_adj(0, hh, true);
   }
 
+  // ---- vmf (direct integration): see oracle/ttn.py vmf_rhs / step_vmf ----
+  void copy64(double2* dst, const double2* src, int64_t n) {
+    run(3, 0.0, [&] { launch_copy(dst, nullptr, src, n, s); });
+  }
+  // node derivative of u into K (flat layout); root: H A, others: the
+  // projected, regularised equation (vmf.cu)
+  void vmf_node(int u, double2* K) {
+    double2* Ku = K + h->node_off[u];
+    store(0, p.node_flow[u].first[0]);
+    apply(0, p.node_flow[u].combine[0],
+          Epi{EPI_RK1, h->h_bufs[u], h->h_bufs_lo[u], h->h_bufs_lo[p.buf.ys], Ku, 0.0});
+    if (u == 0) return;
+    apply(0, p.node_down[u], Epi{EPI_RK1, h->h_bufs[u], h->h_bufs_lo[u], h->h_bufs_lo[p.buf.ys], h->h_bufs[p.buf.acc], 0.0});
+    const int r = p.dims[u][0];
+    const int64_t nc = p.P[u] / r;
+    run(3, 0.0, [&] {
+      launch_vmf_finish(Ku, h->h_bufs[p.buf.acc], h->vmf_dmi, h->h_bufs[u], r, nc, h->vmf_x, s);
+    });
+  }
+  // buffer pn holds the gauge-moved V_pn (the parent edge's class slots the
+  // isometric environments); every child edge gets its isometric environments
+  // and its R, then each child (its own V absorbed) recursively, then the
+  // child's edge is transformed and the child's derivative computed
+  void vmf_walk(int pn, double2* K) {
+    const auto& ch = p.tree.children[pn];
+    for (int c : ch) {
+      copy64(h->vmf_tmp, h->h_bufs[pn], p.P[pn]);
+      qr(pn, c);
+      env(pn, c);
+      copy64(h->vmf_r + h->vmf_r_off[c], h->h_bufs[p.buf.bond_y], (int64_t)p.ranks[c] * p.ranks[c]);
+      copy64(h->h_bufs[pn], h->vmf_tmp, p.P[pn]);
+    }
+    for (int c : ch) {
+      copy64(h->vmf_save + h->node_off[c], h->h_bufs[c], p.P[c]);
+      copy64(h->h_bufs[p.buf.bond_y], h->vmf_r + h->vmf_r_off[c], (int64_t)p.ranks[c] * p.ranks[c]);
+      absorb(c, pn);
+      vmf_walk(c, K);
+      copy64(h->h_bufs[c], h->vmf_save + h->node_off[c], p.P[c]);
+      const int e = p.dir_id(pn, c);
+      const int nk = h->vmf_slot_off[e + 1] - h->vmf_slot_off[e];
+      run(3, 0.0, [&] {
+        launch_vmf_edge((double2* const*)h->T.mats, h->vmf_slots + h->vmf_slot_off[e], nk, h->vmf_r + h->vmf_r_off[c],
+                        p.ranks[c], h->params.vmf_atol, h->vmf_aug, h->vmf_dmi, h->vmf_ctmp, s);
+      });
+      vmf_node(c, K);
+    }
+  }
+  // K := F(t, y) for the stage state in the node buffers
+  void vmf_rhs(double t, double2* K) {
+    drive(t);
+    for (int c : p.tree.postorder)
+      if (c != 0) env(c, p.tree.parent[c]);
+    vmf_node(0, K);
+    vmf_walk(0, K);
+  }
+
   void rebuild_envs() {
     drive(h->t);
     for (int c : p.tree.postorder)
@@ -843,6 +948,8 @@ ttn_status upload_initial(ttn_t h, const double* rho0) {
   (void)s;
   h->envs_dirty = true;
   h->t = 0.0;
+  h->vmf_h = 0.0;
+  h->mix_switched = false;
   return TTN_OK;
 }
 
@@ -897,7 +1004,8 @@ ttn_status ttn_set_params(ttn_t h, const ttn_params* prm) {
     if (!prm) return h->fail(TTN_EINVAL, "null params");
     if (!(prm->qr_tol >= 0) || !(prm->kappa > 0) || !(prm->ps2_atol >= 0) || !(prm->ps2_ratio >= 1) ||
         prm->max_rank < 1 || !(prm->svd_tol >= 0) || prm->max_split < 1 || prm->max_split > kMaxSplit ||
-        (prm->tensor_cores < 0 || prm->tensor_cores > 2) || !(prm->wait_s >= 0.0 && prm->wait_s <= 60.0))
+        (prm->tensor_cores < 0 || prm->tensor_cores > 2) || !(prm->wait_s >= 0.0 && prm->wait_s <= 60.0) ||
+        !(prm->ode_rtol > 0.0) || !(prm->ode_atol > 0.0) || !(prm->vmf_atol >= 0.0))
       return h->fail(TTN_EINVAL, "parameter out of range");
     if (h->ws_bound && prm->max_rank != h->params.max_rank)
       return h->fail(TTN_ESTATE, "max_rank must be set before the workspace is bound");
@@ -1050,6 +1158,26 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
     h->rdm_off = L.rdm_off;
     h->rho_dev = (double2*)(base + L.rho);
     h->flag_dev = (int*)(base + L.flag);
+    h->node_off = L.node_off;
+    if (h->prec == PREC_F64) {
+      h->vmf_n = L.nodes_elems;
+      h->vmf_y = (double2*)(base + L.vmf_y);
+      h->vmf_save = (double2*)(base + L.vmf_save);
+      for (int k = 0; k < 7; ++k) h->vmf_k[k] = (double2*)(base + L.vmf_k) + (int64_t)k * L.nodes_elems;
+      h->vmf_tmp = (double2*)(base + L.vmf_tmp);
+      h->vmf_r = (double2*)(base + L.vmf_r);
+      h->vmf_aug = (double2*)(base + L.vmf_aug);
+      h->vmf_dmi = (double2*)(base + L.vmf_dmi);
+      h->vmf_x = (double2*)(base + L.vmf_x);
+      h->vmf_ctmp = (double2*)(base + L.vmf_ctmp);
+      h->vmf_slots = (int*)(base + L.vmf_slots);
+      h->vmf_err = (double*)(base + L.vmf_err);
+      h->vmf_r_off = L.vmf_r_off;
+      h->vmf_slot_off = L.vmf_slot_off;
+      if (!L.vmf_slot_host.empty())
+        CUDA_TRY(h, cudaMemcpy(h->vmf_slots, L.vmf_slot_host.data(), L.vmf_slot_host.size() * sizeof(int),
+                               cudaMemcpyHostToDevice));
+    }
     h->T.bufs = (void* const*)(base + L.bufs_tab);
     h->T.mats = (void* const*)(base + L.mats_tab);
     h->T.terms = (const ApTerm*)(base + L.terms);
@@ -1196,12 +1324,131 @@ ttn_status ttn_set_rdo0(ttn_t h, const double* rho0) {
   });
 }
 
+}  // extern "C"
+
+namespace {
+
+// Dormand-Prince 5(4) (Dormand & Prince 1980), the tableau and controller of
+// oracle/ttn.py dopri5: err = sqrt(sum |e / (atol + rtol max(|y|, |y5|))|^2 / n)
+// over the active entries, accept when err <= 1, next trial step
+// h * min(5, max(0.2, 0.9 err^(-1/5))), a shortened landing step keeps the
+// longer trial step.
+constexpr double kDpC[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
+constexpr double kDpA[7][6] = {{0, 0, 0, 0, 0, 0},
+                               {1.0 / 5, 0, 0, 0, 0, 0},
+                               {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+                               {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
+                               {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
+                               {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
+                               {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
+constexpr double kDpB5[7] = {35.0 / 384, 0.0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0.0};
+constexpr double kDpB4[7] = {5179.0 / 57600, 0.0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100,
+                             1.0 / 40};
+
+ttn_status vmf_steps(ttn_t h, double dt, int n_steps) {
+  if (h->prec != PREC_F64) return h->fail(TTN_EUNSUPPORTED, "vmf runs in the FP64 form only");
+  Plan& p = h->plan;
+  cudaStream_t s = h->stream;
+  ttn_status st = ensure_envs(h);
+  if (st != TTN_OK) return st;
+  Exec ex(h);
+  double2* nodes = h->h_bufs[0];
+  const int n = p.tree.n_nodes;
+  // inactive tails of the capacity slots stay zero in every flat vector
+  for (int u = 0; u < n; ++u) {
+    const int64_t slot = (u + 1 < n ? h->node_off[u + 1] : h->vmf_n) - h->node_off[u];
+    if (slot > p.P[u])
+      CUDA_TRY(h, cudaMemsetAsync(nodes + h->node_off[u] + p.P[u], 0, (slot - p.P[u]) * sizeof(double2), s));
+  }
+  for (int k = 0; k < 7; ++k) CUDA_TRY(h, cudaMemsetAsync(h->vmf_k[k], 0, h->vmf_n * sizeof(double2), s));
+  int64_t cnt = 0;
+  for (int u = 0; u < n; ++u) cnt += p.P[u];
+  double2* K[7];
+  for (int k = 0; k < 7; ++k) K[k] = h->vmf_k[k];
+  const double rtol = h->params.ode_rtol, atol = h->params.ode_atol;
+  for (int step = 0; step < n_steps; ++step) {
+    const double t0 = h->t, t1 = t0 + dt;
+    double t = t0, h_try = h->vmf_h > 0.0 ? h->vmf_h : dt;
+    ex.copy64(h->vmf_y, nodes, h->vmf_n);
+    ex.vmf_rhs(t, K[0]);
+    int guard = 0;
+    while (t1 - t > 1e-13 * std::max(1.0, std::fabs(t1))) {
+      if (++guard > 100000) return h->fail(TTN_ENUMERIC, "vmf: dopri5 step limit reached");
+      const bool last = h_try >= t1 - t;
+      const double hh = last ? t1 - t : h_try;
+      for (int i = 1; i < 7; ++i) {
+        VmfComb cb{};
+        cb.n = i;
+        for (int l = 0; l < i; ++l) {
+          cb.c[l] = hh * kDpA[i][l];
+          cb.K[l] = K[l];
+        }
+        ex.run(3, 0.0, [&] { launch_vmf_stage(nodes, h->vmf_y, cb, h->vmf_n, s); });
+        ex.vmf_rhs(t + kDpC[i] * hh, K[i]);
+      }
+      VmfComb ce{};
+      ce.n = 7;
+      for (int l = 0; l < 7; ++l) {
+        ce.c[l] = hh * (kDpB5[l] - kDpB4[l]);
+        ce.K[l] = K[l];
+      }
+      ex.run(3, 0.0, [&] {
+        launch_vmf_err(h->vmf_y, nodes, ce, rtol, atol, h->vmf_n, h->vmf_err, h->vmf_err + 1024, s);
+      });
+      double sum = 0.0;
+      CUDA_TRY(h, cudaMemcpyAsync(&sum, h->vmf_err + 1024, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(h, cudaStreamSynchronize(s));
+      if (ex.err != cudaSuccess) return cuda_fail(h, ex.err, "vmf step");
+      const double err = std::sqrt(sum / (double)std::max<int64_t>(cnt, 1));
+      const double fac = err == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * std::pow(err, -0.2)));
+      if (err <= 1.0) {
+        t = last ? t1 : t + hh;
+        ex.copy64(h->vmf_y, nodes, h->vmf_n);  // y5, already in the node buffers
+        std::swap(K[0], K[6]);
+        ++h->vmf_acc;
+        h_try = last ? std::max(h_try, hh * fac) : hh * fac;
+      } else {
+        ++h->vmf_rej;
+        h_try = hh * fac;
+      }
+    }
+    ex.copy64(nodes, h->vmf_y, h->vmf_n);
+    h->vmf_h = h_try;
+    h->t = t1;
+  }
+  for (int k = 0; k < 7; ++k) h->vmf_k[k] = K[k];
+  h->envs_dirty = true;  // the top-down class slots hold the transformed environments
+  ex.run(3, 0.0, [&] { launch_check_finite(h->h_bufs[0], h->plan.P[0], h->flag_dev, h->stream); });
+  CUDA_TRY(h, cudaGetLastError());
+  return TTN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
   return guarded(h, [&]() -> ttn_status {
     if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
     if (!(std::isfinite(dt)) || dt <= 0 || n_steps < 0) return h->fail(TTN_EINVAL, "bad dt or n_steps");
-    if (scheme == TTN_VMF) return h->fail(TTN_EUNSUPPORTED, "vmf is not implemented");
-    if (scheme != TTN_PS1 && scheme != TTN_PS2) return h->fail(TTN_EINVAL, "unknown scheme");
+    if (scheme != TTN_PS1 && scheme != TTN_PS2 && scheme != TTN_VMF && scheme != TTN_MIX)
+      return h->fail(TTN_EINVAL, "unknown scheme");
+    if (scheme == TTN_VMF) return vmf_steps(h, dt, n_steps);
+    if (scheme == TTN_MIX) {  // ps2 until a bond reaches max_rank, then vmf at those ranks
+      for (int k = 0; k < n_steps; ++k) {
+        if (h->mix_switched) {
+          ttn_status st = vmf_steps(h, dt, 1);
+          if (st != TTN_OK) return st;
+          continue;
+        }
+        ttn_status st = ttn_step(h, dt, TTN_PS2, 1);
+        if (st != TTN_OK) return st;
+        int rmax = 0;
+        for (int u = 1; u < h->plan.tree.n_nodes; ++u) rmax = std::max(rmax, h->plan.ranks[u]);
+        if (rmax >= h->params.max_rank) h->mix_switched = true;
+      }
+      return TTN_OK;
+    }
     if (scheme == TTN_PS2) {
       ttn_status st = ensure_envs(h);
       if (st != TTN_OK) return st;

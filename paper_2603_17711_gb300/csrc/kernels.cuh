@@ -200,4 +200,27 @@ void launch_rsvd_vecs(const double2* Q, int m, int kk, const double2* A, const d
 void launch_write_pair(double2* Uf, float2* Uf_lo, const int* fd, int lf, double2* Us, float2* Us_lo, const int* sd,
                        int ls, const double2* Z, const double2* Cm, int r, bool iso_first, cudaStream_t s);
 
+// Direct integration (vmf.cu), FP64. launch_vmf_edge: on edge p -> c with the
+// QR factor R (r x r, row-major) of the upper part and the class matrices at
+// slots_dev[0..n_classes) (isometric environments on entry): rho = R^H R,
+// rho_reg = rho + eps 1, E~ = rho_reg^-1 R^H E R in place, dmi = rho_reg^-1 rho - 1.
+// aug: 3 r^2, tmp: 2 r^2 per class. launch_vmf_finish: K (node derivative, r x
+// nc, row-major over the parent index) += dmi G_down, then K := (1 - P) K with
+// P the projector onto the rows of U (X: r^2 scratch).
+void launch_vmf_edge(double2* const* mats_dev, const int* slots_dev, int n_classes, const double2* R, int r,
+                     double eps, double2* aug, double2* dmi, double2* tmp, cudaStream_t s);
+void launch_vmf_finish(double2* K, const double2* Gdown, const double2* dmi, const double2* U, int r, int64_t nc,
+                       double2* X, cudaStream_t s);
+// out = y + sum_l c[l] K[l] (flat), and the embedded-pair error
+// sum |sum_l c[l] K[l]|^2 / (atol + rtol max(|y|, |y5|))^2 into *out (block
+// partials in part, 1024 doubles, added in order).
+struct VmfComb {
+  int n;
+  double c[7];
+  const double2* K[7];
+};
+void launch_vmf_stage(double2* out, const double2* y, const VmfComb& cb, int64_t n, cudaStream_t s);
+void launch_vmf_err(const double2* y, const double2* y5, const VmfComb& cb, double rtol, double atol, int64_t n,
+                    double* part, double* out, cudaStream_t s);
+
 }  // namespace ttn

@@ -689,6 +689,7 @@ std::string Plan::build_jobs() {
 
   // node flows
   node_flow.assign(n, {});
+  node_down.assign(n, -1);
   for (int u = 0; u < n; ++u) {
     for (int var = 0; var < 3; ++var) {
       int src = var == 0 ? u : var == 1 ? buf.ys : buf.ys2;
@@ -708,6 +709,14 @@ std::string Plan::build_jobs() {
       std::vector<ApTerm> all = singles;
       for (size_t g = 0; g < pairs.size(); ++g) all.push_back(ApTerm{pairs[g][0], pairs[g][1], buf.t0 + (int)g, 0});
       node_flow[u].combine[var] = add_list({base}, {all});
+      if (var == 0 && u != 0) {
+        std::vector<ApTerm> down;
+        for (const ApTerm& t : singles)
+          if (t.leg != 0) down.push_back(t);
+        for (size_t g = 0; g < pairs.size(); ++g)
+          if (pairs[g][1] != 0 && pairs[g][3] != 0) down.push_back(ApTerm{pairs[g][0], pairs[g][1], buf.t0 + (int)g, 0});
+        node_down[u] = add_list({base}, {down});
+      }
     }
   }
   // bond flows (R as a (1, r, r) tensor: leg 1 = from side, leg 2 = to side)

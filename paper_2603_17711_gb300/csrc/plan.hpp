@@ -196,6 +196,11 @@ struct Plan {
   std::vector<PjOut> pj_outs;
   std::vector<PjList> pj_lists;
   std::vector<FlowLists> node_flow;          // per node
+  // per non-root node: the combine list of node_flow (source = the node) kept
+  // to the terms with no factor on the parent leg (singles on the other legs,
+  // pairs between the other legs; T_g as written by node_flow.first[0]); the
+  // direct integration (vmf) weights these terms separately
+  std::vector<int> node_down;
   std::vector<FlowLists> bond_flow;          // per directed bond (from -> to)
   std::vector<EnvLists> env;                 // per directed bond
   std::vector<std::array<int, 3>> absorb;    // per node: ApList id for R on leg li

@@ -197,9 +197,10 @@ def test_overflow_is_reported_as_numeric_error(pkg):
     g.close()
 
 
-def test_vmf_status(pkg):
+def test_vmf_in_the_mixed_form_is_unsupported(pkg):
     w = W.spin_boson_tt(depth=3, n_pade=1, rank=2)
-    g = gpu_from(pkg, w)
+    g = pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0,
+                       precision=pkg.TTN_MIXED_FP32)
     with pytest.raises(pkg.TTNError) as e:
         g.ttn_step(w.dt, pkg.TTN_VMF, 1)
     assert e.value.status == 7
