@@ -335,13 +335,34 @@ def ttn_batch_step(handles: Sequence["TTN"], dt: float, scheme: int = TTN_PS1, n
         raise TTNError(st, f"ttn_batch_step: {msg.decode() if msg else ''}")
 
 
+def pad_to_three_legs(parent: Sequence[int], leg_node: Sequence[int], leg_dims: Sequence[int]):
+    """The library's nodes have exactly three legs. A tree with two-leg nodes
+    (e.g. the arm ends of a centred train, Sec. 7.2 custom frames) is given one
+    extra open leg of dimension 1 on each such node, appended after the other
+    legs: no operator acts on it and its only index is the n = 0 state, so the
+    EDO, the generator and rho_S are unchanged. Returns (leg_node, leg_dims)."""
+    n = len(parent)
+    count = [0 if u == 0 else 1 for u in range(n)]
+    for u in range(1, n):
+        count[parent[u]] += 1
+    for u in leg_node:
+        count[u] += 1
+    leg_node, leg_dims = list(leg_node), list(leg_dims)
+    for u in range(n):
+        if count[u] == 2:
+            leg_node.append(u)
+            leg_dims.append(1)
+    return leg_node, leg_dims
+
+
 def from_model(H, baths, depth, parent, leg_node, ranks, rho0=None, drives=(), precision=TTN_FP64,
                params: Optional[dict] = None, device: int = 0, stream=None) -> TTN:
     """Build, load and bind a TTN for the HEOM of system ``H`` with ``baths``
     (objects with Q, beta, dl, bo, n_ltc, scheme) and ``drives`` (objects with
-    V, g(t), bound)."""
+    V, g(t), bound). Two-leg nodes are padded (pad_to_three_legs)."""
     M = np.asarray(H).shape[0]
-    t = TTN(parent, leg_node, [M, M] + list(depth), ranks, precision)
+    leg_node, leg_dims = pad_to_three_legs(parent, leg_node, [M, M] + list(depth))
+    t = TTN(parent, leg_node, leg_dims, ranks, precision)
     if params:
         t.ttn_set_params(**params)
     t.sop_load(heom.heom_sop(H, baths, depth, drives))

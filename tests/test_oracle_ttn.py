@@ -194,3 +194,20 @@ def test_truncated_ps1_converges_with_rank():
         w.ranks = W.uniform_ranks(w.parent, R)
         errs.append(np.max(np.abs(_run(ttn.from_workload(w), w.n_steps, w.dt) - ref)))
     assert errs[0] > errs[1] > errs[2]
+
+
+def test_centred_train_custom_frame_equals_dense_and_other_trees():
+    """The custom frame of Sec. 7.2 (root in the middle of the train, arm ends
+    with two legs): at untruncated ranks it reproduces the dense hierarchy, as
+    the tensor train and the balanced binary tree do (all three span the whole
+    space there)."""
+    w = W.spin_boson_tt(depth=4, n_pade=3, rank=1000)
+    terms = sop.heom_terms(w.H, w.baths, w.depth)
+    ref = dense.propagate(terms, w.rho0, w.depth, 0.01, 20)
+    out = {}
+    for name, (parent, leg_node) in (("centred", W.centred_train(4)), ("tt", W.tensor_train(4)),
+                                     ("btt", W.balanced_binary(4))):
+        st = ttn.TTN(parent, leg_node, w.leg_dims, [0] + [1000] * (len(parent) - 1), terms, w.rho0)
+        out[name] = _run(st, 20, 0.01)
+        assert np.max(np.abs(out[name] - ref)) < 1e-8, name
+    assert any(len(l) == 2 for l in ttn.Tree(*W.centred_train(4)).legs)

@@ -151,6 +151,31 @@ def balanced_binary(K: int) -> Tuple[List[int], List[int]]:
     return parent, leg_node
 
 
+def centred_train(K: int) -> Tuple[List[int], List[int]]:
+    """The custom tensor train of Sec. 7.2 (Listing customtn1): a chain of
+    feature nodes whose junction node -- carrying no feature -- hangs from the
+    root, so the root sits in the middle of the train instead of at an end.
+    Features 0 .. ceil(K/2)-1 lie on the left arm (the one nearest the
+    junction holding the last of them), the rest on the right arm. The arm
+    ends have two legs (their parent bond and one feature). K >= 2."""
+    if K < 2:
+        raise ValueError("K >= 2")
+    parent = [-1, 0]          # root, junction
+    leg_node = [0, 0] + [-1] * K
+    left = (K + 1) // 2
+    prev = 1
+    for k in reversed(range(left)):  # the left arm walks away from the junction
+        parent.append(prev)
+        prev = len(parent) - 1
+        leg_node[2 + k] = prev
+    prev = 1
+    for k in range(left, K):
+        parent.append(prev)
+        prev = len(parent) - 1
+        leg_node[2 + k] = prev
+    return parent, leg_node
+
+
 def uniform_ranks(parent: Sequence[int], r: int) -> List[int]:
     return [0] + [r] * (len(parent) - 1)
 
@@ -371,3 +396,52 @@ def convergence_spin_boson(panel: str = "b", depth: int = 25, rank: int = 40, tr
     return Workload(name=f"convergence spin-boson panel {panel} {tree.upper()} K={K} N={depth} R={rank}",
                     H=H, baths=[bath], depth=[depth] * K, parent=parent, leg_node=leg_node,
                     ranks=uniform_ranks(parent, rank), rho0=rho0, dt=dt, n_steps=n_steps)
+
+
+@dataclasses.dataclass
+class StarBoson:
+    """Wavefunction (ML-MCTDH) model of Sec. 3.2.4 (Listing mctdh): system H,
+    coupling sys_op Q, a bath given by Brownian peaks (lambda, omega_0', eta)
+    at temperature 1/beta, discretised into n_modes harmonic modes up to
+    `cutoff` (the discretisation itself is done by each side), Fock dimension
+    `dim` per mode, initial wavefunction psi0, tree over the modes."""
+    name: str
+    H: np.ndarray
+    Q: np.ndarray
+    bo: List[Tuple[float, float, float]]
+    beta: float
+    cutoff: float
+    n_modes: int
+    dim: int
+    psi0: np.ndarray
+    parent: List[int]
+    leg_node: List[int]
+    ranks: List[int]
+    dt: float
+    n_steps: int
+
+    @property
+    def leg_dims(self) -> List[int]:
+        M = self.H.shape[0]
+        return [M, M] + [self.dim] * self.n_modes
+
+
+def star_boson_mctdh(n_modes: int = 50, dim: int = 8, rank: int = 8, n_steps: int = 200, dt: float = 1.0,
+                     T: float = 300.0, cutoff_cm1: float = 200.0) -> StarBoson:
+    """Listing mctdh: one Brownian peak (lambda 200, eta 10, omega_0' 50 cm^-1)
+    at 300 K, cutoff 200 cm^-1, 50 modes of Fock dimension 8, dt 1 fs, 200 fs,
+    psi0 = (0, 1), the spin-boson H_S and sys_op of Example 1. The thermofield
+    form (modes of positive and negative frequency for the thermal state) is
+    the one the paper's MCTDH uses; the listing's TEDOPA chain is replaced by a
+    star over the modes (same bath correlation up to the discretisation).
+    Legs: 0 = system, 1 = a spectator of the same dimension that no operator
+    touches (the library's root holds two system legs), 2.. = the modes;
+    balanced binary tree over the modes."""
+    c = CM1_TO_RAD_PER_FS
+    H = np.array([[-750.0, 300.0], [300.0, 750.0]], np.complex128) * c
+    parent, leg_node = balanced_binary(n_modes)
+    return StarBoson(name=f"thermofield star boson, {n_modes} modes, dim {dim}, rank {rank}", H=H,
+                     Q=np.diag([-0.5, 0.5]).astype(np.complex128), bo=[(200.0 * c, 50.0 * c, 10.0 * c)],
+                     beta=_kelvin_beta(T), cutoff=cutoff_cm1 * c, n_modes=n_modes, dim=dim,
+                     psi0=np.array([0.0, 1.0], np.complex128), parent=parent, leg_node=leg_node,
+                     ranks=uniform_ranks(parent, rank), dt=dt, n_steps=n_steps)
