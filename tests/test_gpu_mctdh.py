@@ -22,29 +22,35 @@ def pkg():
     return p
 
 
-def _gpu(pkg, w):
+def _gpu(pkg, w, params=None):
     from paper_2603_17711_gb300 import mctdh
     freqs, gs = mctdh.thermofield_modes(w.bo, w.beta, w.cutoff, w.n_modes)
     t = pkg.TTN(w.parent, w.leg_node, w.leg_dims, w.ranks)
+    if params:
+        t.ttn_set_params(**params)
     t.sop_load(mctdh.mctdh_sop(w.H, w.Q, freqs, gs, w.dim))
     t.bind()
     t.ttn_set_rdo0(omctdh.rho0(w.psi0))
     return t
 
 
-def _oracle(w):
+def _oracle(w, params=None):
     freqs, gs = omctdh.modes(w.bo, w.beta, w.cutoff, w.n_modes)
     return ottn.TTN(w.parent, w.leg_node, w.leg_dims, w.ranks, omctdh.terms(w.H, w.Q, freqs, gs, w.dim),
-                    omctdh.rho0(w.psi0))
+                    omctdh.rho0(w.psi0), params=ottn.Params(**(params or {})))
 
 
 @pytest.mark.parametrize("scheme", ["ps1", "vmf"])
 def test_star_boson_wavefunction_against_oracle(pkg, scheme):
     from paper_2603_17711_gb300 import mctdh
     w = W.star_boson_mctdh(n_modes=8, dim=5, rank=6)
-    g, o = _gpu(pkg, w), _oracle(w)
+    params = {"vmf_atol": 1e-8}  # the product start leaves singular single-hole density matrices
+    g, o = _gpu(pkg, w, params), _oracle(w, params)
     code = pkg.TTN_PS1 if scheme == "ps1" else pkg.TTN_VMF
     err = 0.0
+    for _ in range(3):  # direct integration after a few fixed-rank steps, as the paper advises
+        g.ttn_step(w.dt, pkg.TTN_PS1, 1)
+        o.step(w.dt, "ps1")
     for _ in range(10):
         g.ttn_step(w.dt, code, 1)
         o.step(w.dt, scheme)

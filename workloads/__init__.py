@@ -440,8 +440,10 @@ def star_boson_mctdh(n_modes: int = 50, dim: int = 8, rank: int = 8, n_steps: in
     c = CM1_TO_RAD_PER_FS
     H = np.array([[-750.0, 300.0], [300.0, 750.0]], np.complex128) * c
     parent, leg_node = balanced_binary(n_modes)
+    ranks = uniform_ranks(parent, rank)
+    ranks[1] = min(rank, H.shape[0])  # the spectator index stays 0: the root bond needs rank M, not M^2
     return StarBoson(name=f"thermofield star boson, {n_modes} modes, dim {dim}, rank {rank}", H=H,
                      Q=np.diag([-0.5, 0.5]).astype(np.complex128), bo=[(200.0 * c, 50.0 * c, 10.0 * c)],
                      beta=_kelvin_beta(T), cutoff=cutoff_cm1 * c, n_modes=n_modes, dim=dim,
                      psi0=np.array([0.0, 1.0], np.complex128), parent=parent, leg_node=leg_node,
-                     ranks=uniform_ranks(parent, rank), dt=dt, n_steps=n_steps)
+                     ranks=ranks, dt=dt, n_steps=n_steps)
