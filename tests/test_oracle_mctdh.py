@@ -25,6 +25,7 @@ def test_thermofield_modes_reproduce_the_thermal_bcf():
 
 def _tiny(n_modes=4, dim=3):
     w0 = W.star_boson_mctdh(n_modes=n_modes, dim=dim, rank=1000)
+    w0.ranks = [0] + [1000] * (len(w0.parent) - 1)  # untruncated, the root bond included
     w, g = mctdh.modes(w0.bo, w0.beta, w0.cutoff, n_modes)
     terms = mctdh.terms(w0.H, w0.Q, w, g, dim)
     return w0, w, g, terms
