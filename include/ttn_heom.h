@@ -109,10 +109,14 @@ typedef struct {
  *                    thread). Both give the same results bit for bit; on the
  *                    rank-64 chain the ring kernel is ~15 % faster per launch
  *                    but its split pass costs as much as it saves.
- *  wait_s    (2.0)   0..60: upper bound, in seconds, of every device-side wait
- *                    of the kernels whose blocks wait on one another (the grid
- *                    barriers of the Jacobi SVD); a wait that runs out is
- *                    reported as TTN_ETIMEOUT (no counterpart in the paper).
+ *  wait_s    (2.0)   0..60: upper bound, in seconds, of the device-side waits
+ *                    of the kernels whose blocks wait on one another through
+ *                    global memory (the grid barriers of the Jacobi SVD and of
+ *                    the blocked QR's panels over the whole GPU); a wait that
+ *                    runs out is reported as TTN_ETIMEOUT by the next
+ *                    synchronising call and the state is undefined (no
+ *                    counterpart in the paper). The cluster QR's exchanges
+ *                    keep a fixed 2 s bound.
  *  ode_rtol  (1e-5)  vmf: relative and absolute tolerance of the dopri5
  *  ode_atol  (1e-7)  controller (Sec. 4, Table 4 defaults).
  *  vmf_atol  (1e-10) vmf: added to the diagonal of every single-hole density

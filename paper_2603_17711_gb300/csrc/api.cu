@@ -438,7 +438,8 @@ struct Exec {
     const double flops = 8.0 * 2.0 * (2.0 * m * n * n - 2.0 * n * n * n / 3.0);
     run(2, flops, [&] {
       launch_qr(h->h_bufs[u], d[0], d[1], d[2], li, h->params.qr_tol, h->qr_work, h->qr_elems,
-                h->h_bufs[p.buf.tmp], h->h_bufs[p.buf.bond_y], h->flag_dev, lo_copy(u), lo_copy(p.buf.bond_y), s);
+                h->h_bufs[p.buf.tmp], h->h_bufs[p.buf.bond_y], h->flag_dev, lo_copy(u), lo_copy(p.buf.bond_y), s,
+                wait_ns());
     });
   }
   // FP32 shadow of an FP64 buffer (nullptr in FP64 mode, where they coincide)
@@ -1495,7 +1496,7 @@ static ttn_status check_flag(ttn_t h) {
   int flag = 0;
   CUDA_TRY(h, cudaMemcpyAsync(&flag, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  if (flag & 2) return h->fail(TTN_ETIMEOUT, "a cluster or grid exchange of the QR kernels gave up after 2 s");
+  if (flag & 2) return h->fail(TTN_ETIMEOUT, "a cluster or grid exchange of the QR kernels gave up");
   if (flag & 8) return h->fail(TTN_ETIMEOUT, "a tensor-core MMA wait gave up after 1 s");
   if (flag & 16) return h->fail(TTN_ETIMEOUT, "a grid barrier of the Jacobi SVD gave up after wait_s");
   if (flag) return h->fail(TTN_ENUMERIC, "non-finite amplitude in the root tensor");

@@ -623,9 +623,11 @@ __global__ void __launch_bounds__(kQrThreads) k_qr(double2* U, int d0, int d1, i
 }
 
 void launch_qr(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work, int64_t work_elems,
-               double2* qbuf, double2* R, int* flag, float2* U_lo, float2* R_lo, cudaStream_t s) {
+               double2* qbuf, double2* R, int* flag, float2* U_lo, float2* R_lo, cudaStream_t s,
+               uint64_t grid_wait_ns) {
   if (launch_qr_cluster(U, d0, d1, d2, leg, tol, R, flag, U_lo, R_lo, work, work_elems, s)) return;
-  if (launch_qr_blocked(U, d0, d1, d2, leg, tol, work, work_elems, qbuf, R, flag, U_lo, R_lo, s)) return;
+  if (launch_qr_blocked(U, d0, d1, d2, leg, tol, work, work_elems, qbuf, R, flag, U_lo, R_lo, s, grid_wait_ns))
+    return;
   k_qr<<<1, kQrThreads, 0, s>>>(U, d0, d1, d2, leg, tol, work, qbuf, R, flag, U_lo, R_lo);
 }
 

@@ -105,8 +105,13 @@ bool launch_project_tiled(int prec, const DevTables& T, const PjList& L, int d, 
 // qr_blocked_elems(m, n) of it; otherwise P suffices). Tried in order: the
 // cluster kernel (n <= 64, rows fit a cluster), the blocked path (n <= 64),
 // the one-CTA kernel (any n).
+// grid_wait_ns: bound of the grid barriers of the blocked path's panels over
+// the whole GPU, counted from the panel kernel's start (the cluster kernel's
+// exchanges keep a fixed 2 s: a CTA that gave up there could leave a peer's
+// asynchronous store into its shared memory in flight).
 void launch_qr(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work, int64_t work_elems,
-               double2* qbuf, double2* R, int* flag, float2* U_lo, float2* R_lo, cudaStream_t s);
+               double2* qbuf, double2* R, int* flag, float2* U_lo, float2* R_lo, cudaStream_t s,
+               uint64_t grid_wait_ns = 2000000000ull);
 // Cluster-parallel variant (qr.cu); returns false when the shape does not fit
 // (bond dim > kQrClusterMaxN or the row blocks exceed shared memory).
 constexpr int kQrClusterMaxN = 64;
@@ -141,7 +146,7 @@ int qr_panel_cluster(int m_act, int nb);  // cluster size of a panel, 0 if it do
 int64_t qr_blocked_elems(int64_t m, int64_t n);
 bool launch_qr_blocked(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work,
                        int64_t work_elems, double2* qbuf, double2* R, int* flag, float2* U_lo, float2* R_lo,
-                       cudaStream_t s);
+                       cudaStream_t s, uint64_t grid_wait_ns = 2000000000ull);
 // dst = src (FP64); dst_lo (nullable) = FP32 copy.
 void launch_copy(double2* dst, float2* dst_lo, const double2* src, int64_t n, cudaStream_t s);
 // rho / vector contraction for one node: out[a] (non-root) or out[i*d1+j] (root)

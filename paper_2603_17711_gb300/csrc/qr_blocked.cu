@@ -301,11 +301,14 @@ __device__ bool grid_arrive_wait(unsigned* bar, unsigned target, bool wait, uint
 // and R entries above written back to A, per-column beta / alpha / phase /
 // skip, and the panel's WY factor T from T^{-1} = diag(1/beta) +
 // strictly-upper(V^H V) (partial Grams reduced over the grid, back substitution
-// in CTA 0). Every wait is bounded (2 s): bit 2 of *flag on expiry.
+// in CTA 0). Every wait is bounded (wait_ns from the kernel's start, 2 s by
+// default): bit 2 of *flag on expiry; the CTA then skips its remaining waits
+// and runs to its end (it only exchanges through global memory, so no peer
+// can still be writing into its shared memory when it exits).
 __global__ void __launch_bounds__(256) k_qb_panel_grid(double2* A, int64_t m, int c0, int nb, const double* sc,
                                                        double* beta, double* alpha, double2* phase, int* skip,
                                                        double2* T, double2* rec, double2* own, double2* gp,
-                                                       double2* gf, unsigned* bar, int* flag) {
+                                                       double2* gf, unsigned* bar, int* flag, uint64_t wait_ns) {
   __shared__ double2 X[kNB][kPgRows];  // my rows of the panel, column-major
   __shared__ double2 red[kNB];         // this column's summed record: [0].x = |x|^2, [t] = sum u_{j+t}
   __shared__ double2 s_own[kNB];       // [0] = x_0, [t] = a_{j+t}[j]
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(256) k_qb_panel_grid(double2* A, int64_t m, in
   const int rp = (int)((Rrows + G - 1) / G);
   const int64_t r0 = (int64_t)me * rp;
   const int nr = (int)max((int64_t)0, min(Rrows, r0 + rp) - r0);
-  const uint64_t deadline = gtimer() + 2000000000ull;
+  const uint64_t deadline = gtimer() + wait_ns;
   bool alive = true;
   for (int t = tid; t < nb * rp; t += blockDim.x) {
     const int c = t / rp, i = t % rp;
@@ -523,7 +526,7 @@ int64_t qr_blocked_elems(int64_t m, int64_t n) { return qb_layout(m, n).total; }
 
 bool launch_qr_blocked(double2* U, int d0, int d1, int d2, int leg, double tol, double2* work,
                        int64_t work_elems, double2* qbuf, double2* R, int* flag, float2* U_lo, float2* R_lo,
-                       cudaStream_t s) {
+                       cudaStream_t s, uint64_t grid_wait_ns) {
   const int dd[3] = {d0, d1, d2};
   const int n = dd[leg];
   const int64_t m = (int64_t)d0 * d1 * d2 / n;
@@ -569,7 +572,7 @@ bool launch_qr_blocked(double2* U, int d0, int d1, int d2, int leg, double tol, 
       cfg.numAttrs = 1;
       return cudaLaunchKernelEx(&cfg, k_qb_panel_grid, A, (int64_t)m, pn.c0, pn.nb, (const double*)sc, beta, alpha,
                                 phase, skip, pn.T, work + L.rec, work + L.own, work + L.gp, work + L.gf, bar + 8 * idx,
-                                flag) == cudaSuccess;
+                                flag, grid_wait_ns) == cudaSuccess;
     }
     return launch_qr_panel(pn, s);
   };

@@ -1,0 +1,67 @@
+"""Failure detection in the admitted form: bounded device waits. With the wait
+limit set to zero, the grid barriers of the blocked QR's whole-GPU panels and
+of the whole-GPU Jacobi SVD give up at their first unsuccessful poll; the
+kernels record it in the device flag and run to their end (they exchange only
+through global memory, so no CTA leaves while a peer could still write into
+its shared memory), the library reports TTN_ETIMEOUT, and the same process then
+propagates a fresh handle correctly. No GPU fault, trap or hang is involved."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ttn as ottn
+
+pytestmark = pytest.mark.gpu
+
+TTN_ETIMEOUT = 5
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2603_17711_gb300 as p
+    p.library()
+    return p
+
+
+def test_grid_panel_qr_zero_wait_then_fresh_handle(pkg):
+    w = W.exciton_chain(n_sites=4, depth=4, rank=64)  # a 64 x 64 x 64 node: 4096 x 64 matricisations
+    g = pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0)
+    assert any(int(np.prod(g.ttn_node_shape(u))) >= 4096 * 64 for u in range(len(w.parent)))
+    g.ttn_set_params(wait_s=0.0)
+    with pytest.raises(pkg.TTNError) as e:
+        g.ttn_step(w.dt, pkg.TTN_PS1, 1)
+        g.ttn_rdm()
+    assert e.value.status == TTN_ETIMEOUT
+    g.close()
+    # the context is intact: a fresh handle follows the oracle
+    g = pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0)
+    o = ottn.from_workload(w)
+    g.ttn_step(w.dt, pkg.TTN_PS1, 1)
+    o.step(w.dt, "ps1")
+    err = float(np.max(np.abs(g.ttn_rdm() - o.rdm())))
+    g.close()
+    assert err <= 1e-10, err
+
+
+def test_grid_jacobi_zero_wait_in_ps2_then_fresh_handle(pkg):
+    w = W.driven_structured_tls(n_pade=1, depth=10, cap=32)
+    params = {"max_rank": 32, "ps2_atol": 1e-6, "wait_s": 0.0}
+    g = pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0, drives=w.drives,
+                       params=params)
+    with pytest.raises(pkg.TTNError) as e:
+        for _ in range(20):  # the two-site matrices reach 24 columns within a few steps
+            g.ttn_step(w.dt, pkg.TTN_PS2, 1)
+    assert e.value.status == TTN_ETIMEOUT
+    g.close()
+    params["wait_s"] = 2.0
+    g = pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0, drives=w.drives,
+                       params=params)
+    o = ottn.from_workload(w, params=ottn.Params(ps2_atol=1e-6, max_rank=32))
+    for _ in range(3):
+        g.ttn_step(w.dt, pkg.TTN_PS2, 1)
+        o.step(w.dt, "ps2")
+    err = float(np.max(np.abs(g.ttn_rdm() - o.rdm())))
+    g.close()
+    assert err <= 1e-10, err
