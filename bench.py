@@ -441,6 +441,27 @@ def paper_models_leg(pkg, torch, local_rank, flush, sweeps: bool) -> dict:
         return np.array(out)
 
     res = {}
+    # ML-MCTDH on the same machinery (Sec. 3.2.4): the thermofield star bath of the listing
+    from paper_2603_17711_gb300 import mctdh
+    sb = W.star_boson_mctdh()
+    fr, gs = mctdh.thermofield_modes(sb.bo, sb.beta, sb.cutoff, sb.n_modes)
+    g = pkg.TTN(sb.parent, sb.leg_node, sb.leg_dims, sb.ranks)
+    g.sop_load(mctdh.mctdh_sop(sb.H, sb.Q, fr, gs, sb.dim))
+    g.bind(local_rank)
+    r0 = np.zeros((2, 2), np.complex128)
+    r0[:, 0] = sb.psi0
+    g.ttn_set_rdo0(r0)
+    g.ttn_step(sb.dt, 1, 2)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(g.stream)
+    g.ttn_step(sb.dt, 1, sb.n_steps)
+    b.record(g.stream)
+    b.synchronize()
+    rho = mctdh.rho_from_root(g.ttn_get_node(0).reshape(2, 2, -1))
+    g.close()
+    res["mctdh_star_boson"] = {"workload": sb.name + ", ps1, dt 1 fs, 200 steps", "steps_per_s":
+                               sb.n_steps / (a.elapsed_time(b) * 1e-3), "population_1_at_202_fs": float(rho[1, 1].real)}
     w = W.structured_spin_boson()
     sps, rho = timed(w, 1000)
     res["structured_spin_boson"] = {"workload": w.name + ", dt 1 fs, 1000 steps, ps1 FP64", "steps_per_s": sps,
@@ -468,6 +489,39 @@ def paper_models_leg(pkg, torch, local_rank, flush, sweeps: bool) -> dict:
         res["table2_note"] = ("mean over 1000 steps (1 fs) of |rho_11 - rho_11(reference)|; panel a: depth sweep "
                               "against depth 25 (BTT, rank 40); panels b, c: rank sweep against rank 40 at depth 8")
     return res
+
+
+def vmf_leg(pkg, torch, local_rank) -> dict:
+    """Direct integration (vmf, dopri5 with ode_rtol 1e-5 / ode_atol 1e-7) of the
+    7-site chain at rank 20 after 20 ps1 steps, against ps1 continued over the
+    same 20 steps, and the mix strategy (ps2 then vmf) on the adaptive-rank
+    workload."""
+    w = W.exciton_chain()
+    ga, gb = make_gpu(pkg, w, local_rank), make_gpu(pkg, w, local_rank)
+    ga.ttn_step(w.dt, 1, 20)
+    gb.ttn_step(w.dt, 1, 20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ga.ttn_step(w.dt, pkg.TTN_VMF, 20)
+    ra = ga.ttn_rdm()
+    el = time.perf_counter() - t0
+    gb.ttn_step(w.dt, 1, 20)
+    rb = gb.ttn_rdm()
+    ga.close()
+    gb.close()
+    out = {"workload": "7-site chain at rank 20 (as the headline), 20 vmf steps after 20 ps1 steps",
+           "steps_per_s": 20 / el, "rdm_max_abs_vmf_vs_ps1": float(np.max(np.abs(ra - rb))),
+           "timing": "host wall clock (the step control synchronises)"}
+    wm = W.driven_structured_tls(n_pade=1, depth=10, cap=16)
+    g = pkg.from_model(wm.H, wm.baths, wm.depth, wm.parent, wm.leg_node, wm.ranks, rho0=wm.rho0, drives=wm.drives,
+                       device=local_rank, params={"max_rank": 16, "ps2_atol": 1e-6})
+    t0 = time.perf_counter()
+    g.ttn_step(wm.dt, pkg.TTN_MIX, 40)
+    g.ttn_rdm()
+    out["mix"] = {"workload": "driven TLS, structured bath, K = 8, depth 10, ps2 (atol 1e-6, cap 16) then vmf, 40 steps",
+                  "steps_per_s": 40 / (time.perf_counter() - t0), "ranks_at_end": [int(x) for x in g.ttn_get_ranks()]}
+    g.close()
+    return out
 
 
 def bench_ours(args, rank, world, local_rank):
@@ -568,6 +622,7 @@ def bench_ours(args, rank, world, local_rank):
     c1 = config1_leg(pkg, torch, local_rank, flush)
     # ---- the paper's example models (throughput; the sweeps run with --paper-only) ----
     pm = paper_models_leg(pkg, torch, local_rank, flush, False)
+    vm = vmf_leg(pkg, torch, local_rank)
     # ---- adaptive rank: SVD rule against the learned rank proposer ----
     p2 = None if args.no_ps2 else ps2_leg(args, pkg, torch, local_rank)
 
@@ -711,6 +766,7 @@ def bench_ours(args, rank, world, local_rank):
         "config1_spin_boson_tt": c1,
         "ps2_learned_rank": p2,
         "paper_models": pm,
+        "vmf": vm,
         "peaks": peaks,
         "gpu_launches": launches,
         "clocks": clk.summary(),
