@@ -480,14 +480,12 @@ def paper_models_leg(pkg, torch, local_rank, flush, sweeps: bool) -> dict:
             str(d): float(np.mean(np.abs(traj(W.convergence_spin_boson("a", depth=d, rank=40), n) - ref_a)))
             for d in (2, 4, 6, 10, 14)}
         for tree in ("btt", "tt"):
-            # depth 8: the truncated hierarchy of this model is unstable from depth 12 on (the
-            # dense generator's spectral abscissa is -0.0015 /fs at depth 8, +0.0055 /fs at depth 12)
-            ref = traj(W.convergence_spin_boson("b", depth=8, rank=40, tree=tree), n)
+            ref = traj(W.convergence_spin_boson("b", depth=25, rank=40, tree=tree), n)
             res[f"table2_rank_sweep_{tree}"] = {
-                str(r): float(np.mean(np.abs(traj(W.convergence_spin_boson("b", depth=8, rank=r, tree=tree), n) - ref)))
+                str(r): float(np.mean(np.abs(traj(W.convergence_spin_boson("b", depth=25, rank=r, tree=tree), n) - ref)))
                 for r in (2, 4, 8, 12, 16, 24, 32)}
         res["table2_note"] = ("mean over 1000 steps (1 fs) of |rho_11 - rho_11(reference)|; panel a: depth sweep "
-                              "against depth 25 (BTT, rank 40); panels b, c: rank sweep against rank 40 at depth 8")
+                              "against depth 25 (BTT, rank 40); panels b, c: rank sweep against rank 40 at depth 25")
     return res
 
 

@@ -375,17 +375,20 @@ def convergence_spin_boson(panel: str = "b", depth: int = 25, rank: int = 40, tr
     panel 'a' -- symmetric (Delta eps = 0, V = 300 cm^-1), Drude-Lorentz bath
     only (540, 70 cm^-1), coupled through sigma_x (the depth sweep);
     panel 'b' -- Delta eps = 1500, V = 300, Drude-Lorentz (540, 70) plus a
-    Brownian peak (lambda 330, eta 4, omega_0' 1663), coupled through sigma_z
-    (the rank sweeps, BTT and TT). Temperature, Pade correction, dt and the
-    initial state follow the Example 1 listing (300 K, n_ltc 1, 1 fs,
-    rho0 = |1><1|)."""
+    Brownian peak (lambda 330, eta 4, omega_0' 1663) (the rank sweeps, BTT and
+    TT), with the system Hamiltonian and coupling of the Example 1 listing.
+    The coupling carries the factor 1/2 of H_SB = (sigma_z / 2) X_B of
+    Sec. 3.2 in both panels (the listing's sys_op diag(-1/2, 1/2); sigma_x / 2
+    in panel a); the text's later shorthand "sigma ⊗ X_B" is read as the same
+    convention. Temperature, Pade correction, dt and the initial state follow
+    the Example 1 listing (300 K, n_ltc 1, 1 fs, rho0 = |1><1|)."""
     c = CM1_TO_RAD_PER_FS
     if panel == "a":
         H = 300.0 * SIGMA_X * c
-        bath = Bath(Q=SIGMA_X.copy(), beta=_kelvin_beta(T), dl=(540.0 * c, 70.0 * c), n_ltc=n_ltc)
+        bath = Bath(Q=0.5 * SIGMA_X, beta=_kelvin_beta(T), dl=(540.0 * c, 70.0 * c), n_ltc=n_ltc)
     elif panel == "b":
         H = (np.array([[-750.0, 0.0], [0.0, 750.0]]) + 300.0 * SIGMA_X.real).astype(np.complex128) * c
-        bath = Bath(Q=SIGMA_Z.copy(), beta=_kelvin_beta(T), dl=(540.0 * c, 70.0 * c),
+        bath = Bath(Q=np.diag([-0.5, 0.5]).astype(np.complex128), beta=_kelvin_beta(T), dl=(540.0 * c, 70.0 * c),
                     bo=[(330.0 * c, 1663.0 * c, 4.0 * c)], n_ltc=n_ltc)
     else:
         raise ValueError(panel)
