@@ -631,6 +631,8 @@ def bench_ours(args, rank, world, local_rank):
         hs = [make_gpu(pkg, bw, local_rank) for bw in bws]
         for hh in hs:  # concurrent instances fill the GPU: one CTA per output tile
             hh.ttn_set_params(max_split=1)
+        # warps per CTA of the whole batch, by timing (states put back afterwards)
+        tune_b = pkg.ttn_batch_autotune(hs, 0.01, 2)
         pkg.ttn_batch_step(hs, 0.01, 1, args.warmup)
         torch.cuda.synchronize()
         s0 = hs[0].stream
@@ -649,6 +651,7 @@ def bench_ours(args, rank, world, local_rank):
         hm = [make_gpu(pkg, bw, local_rank, precision=pkg.TTN_MIXED_FP32) for bw in bws]
         for hh in hm:
             hh.ttn_set_params(max_split=1)
+        tune_m = pkg.ttn_batch_autotune(hm, 0.01, 2)
         pkg.ttn_batch_step(hm, 0.01, 1, args.warmup)
         torch.cuda.synchronize()
         with torch.cuda.stream(hm[0].stream):
@@ -679,6 +682,9 @@ def bench_ours(args, rank, world, local_rank):
                      "ms_per_batched_step": ms_b / args.steps,
                      "sequential_instance_steps_per_s": args.batch * n_seq / seq_s,
                      "node_contraction_gflop_per_batched_step": k1 / 1e9,
+                     "tile_shape": {"how": "ttn_batch_autotune: warps per CTA of every contraction list "
+                                           "(8 / 4 / 2) chosen by timing 2 batched steps each; states put back",
+                                    "fp64": tune_b, "mixed_fp32": tune_m},
                      "mixed_fp32": {"instance_steps_per_s": args.batch * args.steps / (ms_bm * 1e-3),
                                     "ms_per_batched_step": ms_bm / args.steps,
                                     "rdm_max_abs_vs_fp64_batch": max(errs),

@@ -120,7 +120,14 @@ typedef struct {
  *  ode_rtol  (1e-5)  vmf: relative and absolute tolerance of the dopri5
  *  ode_atol  (1e-7)  controller (Sec. 4, Table 4 defaults).
  *  vmf_atol  (1e-10) vmf: added to the diagonal of every single-hole density
- *                    matrix before it is inverted (Sec. 7.5 regularisation). */
+ *                    matrix before it is inverted (Sec. 7.5 regularisation).
+ *  tile_warps (0)    0, 2, 4 or 8: warps per CTA sharing one 32-output tile of
+ *                    the CUDA-core contraction launches (0: 8). Setting it (or
+ *                    max_split) replaces the launch shapes of every job list
+ *                    by the planned ones; ttn_autotune then picks warps and
+ *                    split per list. Fewer warps per tile waste less on idle
+ *                    warps and reductions when many instances run at once
+ *                    (no counterpart in the paper). */
 typedef struct {
   double qr_tol;
   double kappa;
@@ -134,6 +141,7 @@ typedef struct {
   double ode_rtol;
   double ode_atol;
   double vmf_atol;
+  int32_t tile_warps;
 } ttn_params;
 
 /* Create a handle (Sec. 2.3, Eq. omega_tensor). leg_dims[n_legs]: leg
@@ -353,17 +361,48 @@ ttn_status ttn_rdm_noalloc(const ttn_tree* tree, const int32_t* leg_dims, const 
                            size_t err_len);
 
 /* Autotuner (no counterpart in the paper: GB300 work distribution). Times
- * every contraction job list of the handle on its stream with each admissible
- * split (1 .. min(useful, max_split) CTAs per output tile; reps timed launches
- * each, after one warm-up) and keeps the fastest (a larger split must win by
- * 3 %). The state is not modified: scratch-writing lists run as they are, RK4
- * epilogue lists run as stage 1 into scratch, and the environment matrices the
- * projections overwrite are rebuilt before the next step. Results stay within
- * rounding of the untuned ones (reduction orders change with the split) and
- * are deterministic for a given tuning. Changing max_split, or a ps2 rank
- * change rebuilding a list, returns those lists to the built-in rule.
- * reps: 1..100. Errors: TTN_ESTATE before ttn_set_workspace, TTN_EINVAL. */
+ * every CUDA-core contraction job list of the handle on its stream with each
+ * admissible tile shape -- warps per CTA w in {8, 4, 2} sharing one 32-output
+ * tile, times the split k = 1 .. min(useful(w), max_split) CTAs (one cluster)
+ * per tile -- and keeps the fastest (another shape must win by 3 %); the
+ * environment projections get the split only. Lists with the same key (see
+ * ttn_tuning_get) are timed once and share the shape. reps timed launches per shape,
+ * after one warm-up. The state is not modified: scratch-writing lists run as
+ * they are, RK4 epilogue lists run as stage 1 into scratch, and the
+ * environment matrices the projections overwrite are rebuilt before the next
+ * step. Results stay within rounding of the untuned ones (reduction orders
+ * change with the shape) and are deterministic for a given tuning. Changing
+ * max_split or tile_warps, or a ps2 rank change rebuilding a list, returns
+ * those lists to the planned shapes. reps: 1..100. Errors: TTN_ESTATE before
+ * ttn_set_workspace, TTN_EINVAL. */
 ttn_status ttn_autotune(ttn_t h, int32_t reps);
+
+/* Tile shapes of the job lists, for caching a tuning across runs. Each list is
+ * one row of TTN_TUNING_COLS int32: kind (0 contraction, 1 environment
+ * projection), precision of the list (0 FP64, 1 FP32), the shape of its first
+ * output (d0, d1, d2, d3; for projections d0, d1, d2 and the open leg), its
+ * number of outputs, of terms (0 for projections) and of output tiles -- the
+ * key of the row, 9 values -- then w (warps per CTA) and k (CTAs per tile).
+ * ttn_tuning_get writes min(n_lists, max_rows) rows to rows (nullable when
+ * max_rows is 0) and the number of lists to *n_rows. ttn_tuning_set gives
+ * every list whose key equals a row's key that row's shape (the first such
+ * row); *n_applied (nullable) = lists set. Rows with w not in {2, 4, 8} (8 for
+ * projections) or k outside 1..max_split are refused with TTN_EINVAL before
+ * anything is set. Errors: TTN_ESTATE before sop_load, TTN_EINVAL. */
+#define TTN_TUNING_COLS 11
+
+/* Tile shape of a batch (no counterpart in the paper): times reps batched ps1
+ * steps of the handles (ttn_batch_step, after one untimed step that captures
+ * the graphs) with tile_warps = 8, 4 and 2 on every member, keeps the fastest
+ * (another must win by 3 %) and puts every member's state back (checkpoint
+ * blobs in host memory), so the batch continues from where it was. The members'
+ * lists get the planned shapes for that warp count. *warps_out (nullable): the
+ * warps chosen; ms_out (nullable, 3 floats): ms per batched step for 8, 4, 2.
+ * Synchronises the members' streams. Errors: as ttn_batch_step, TTN_EINVAL for
+ * reps outside 1..100. */
+ttn_status ttn_batch_autotune(ttn_t* hs, int32_t n, double dt, int32_t reps, int32_t* warps_out, float* ms_out);
+ttn_status ttn_tuning_get(ttn_t h, int32_t* rows, int32_t max_rows, int32_t* n_rows);
+ttn_status ttn_tuning_set(ttn_t h, const int32_t* rows, int32_t n_rows, int32_t* n_applied);
 
 /* Singular value decomposition a = U diag(sigma) V^H of a device matrix by
  * one-sided (Hestenes) Jacobi rotations in FP64: the factorisation the ps2
@@ -372,10 +411,11 @@ ttn_status ttn_autotune(ttn_t h, int32_t reps);
  * min(m, n). Outputs: u_dev m x k and vh_dev k x n (device, row-major), sigma_host
  * k values in descending order; singular vectors of sigma = 0 are returned as
  * zero. ws_dev: ttn_svd_workspace_size(m, n) bytes, 256-byte aligned. Matrices
- * whose smaller side has 24 or more columns run over the whole GPU (the pairs
- * of each round of the circle ordering spread over the CTAs of one cooperative
- * launch, one grid barrier per round); every barrier wait is bounded by
- * wait_s seconds (0..60). *sweeps_out (nullable): sweeps that rotated.
+ * whose smaller side has more than 16 columns run over several CTAs (the pairs
+ * of each round of the circle ordering spread over the CTAs, one barrier per
+ * round: a thread-block cluster's up to 32 columns, else a cooperative launch
+ * over the whole GPU); every grid barrier wait is bounded by wait_s seconds
+ * (0..60). *sweeps_out (nullable): sweeps that rotated.
  * Synchronises `stream` (cudaStream_t as void*). Errors: TTN_EINVAL,
  * TTN_ENOMEM (workspace too small or misaligned), TTN_ETIMEOUT (a barrier
  * wait gave up; outputs undefined), TTN_ENUMERIC (no convergence within 60

@@ -8,6 +8,8 @@ PyTorch device memory and streams. There is no CPU fallback: constructing a
 from __future__ import annotations
 
 import ctypes as C
+import json
+import os
 from typing import Callable, Optional, Sequence
 
 import numpy as np
@@ -18,9 +20,10 @@ from ._lib import (DRIVE_FN, TTN_FP64, TTN_MIXED_FP32, TTN_MIX, TTN_OK, TTN_PS1,
 from . import _lib
 
 __all__ = ["TTN", "TTNError", "heom", "TTN_FP64", "TTN_MIXED_FP32", "TTN_PS1", "TTN_PS2", "TTN_VMF", "TTN_MIX",
-           "library", "from_model", "ttn_batch_step", "RankProposer"]
+           "library", "from_model", "ttn_batch_step", "ttn_batch_autotune", "RankProposer"]
 
 _LIB: Optional[C.CDLL] = None
+_TUNING_FORMAT = "ttn-heom tile shapes 1"
 
 
 def library() -> C.CDLL:
@@ -52,6 +55,7 @@ class TTN:
         self.n_nodes = len(self._parent)
         self._drive_cbs = []
         self._ws = None
+        self.device = 0
 
     # -- plumbing -----------------------------------------------------------
     def _check(self, st: int, what: str) -> None:
@@ -110,6 +114,7 @@ class TTN:
         if not torch.cuda.is_available():
             raise RuntimeError("TTN needs a CUDA device: the library has no CPU path")
         dev = torch.device("cuda", device)
+        self.device = device
         n = self.ttn_workspace_size()
         self._ws = torch.empty(n + 256, dtype=torch.uint8, device=dev)
         base = self._ws.data_ptr()
@@ -207,8 +212,57 @@ class TTN:
     def ttn_stats_reset(self) -> None:
         self._check(self.lib.ttn_stats_reset(self.h), "ttn_stats_reset")
 
-    def ttn_autotune(self, reps: int = 3) -> None:
+    def ttn_autotune(self, reps: int = 3, cache: Optional[str] = None) -> str:
+        """Pick the tile shape (warps per CTA, CTAs per tile) of every job list
+        by timing (ttn_autotune). cache: path of a JSON file of tile shapes
+        keyed by list shape; when it holds a shape for every list of this
+        handle on this device those are used as they are ("cache"), else the
+        lists are timed ("tuned") and their shapes merged into the file."""
+        dev = self._device_tag()
+        old_rows = []
+        if cache is not None and os.path.exists(cache):
+            with open(cache) as f:
+                doc = json.load(f)
+            if doc.get("format") == _TUNING_FORMAT and doc.get("device") == dev:
+                old_rows = [list(map(int, r)) for r in doc.get("rows", [])]
+                if self.ttn_tuning_set(np.asarray(old_rows, np.int32).reshape(-1, _lib.TTN_TUNING_COLS)) == \
+                        len(self.ttn_tuning_get()):
+                    return "cache"
         self._check(self.lib.ttn_autotune(self.h, int(reps)), "ttn_autotune")
+        if cache is not None:
+            mine = self.ttn_tuning_get().tolist()
+            have = {tuple(r[:9]) for r in mine}
+            rows = mine + [r for r in old_rows if tuple(r[:9]) not in have]
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump({"format": _TUNING_FORMAT, "device": dev,
+                           "columns": ["kind", "precision", "d0", "d1", "d2", "d3_or_leg", "outputs", "terms",
+                                       "tiles", "warps", "split"], "rows": rows}, f)
+            os.replace(tmp, cache)
+        return "tuned"
+
+    def _device_tag(self) -> str:
+        import torch
+        pr = torch.cuda.get_device_properties(self.device)
+        return f"{pr.name} / {pr.multi_processor_count} SMs"
+
+    def ttn_tuning_get(self) -> np.ndarray:
+        """Tile shapes of every job list: int32 [n_lists, 11] rows (9 key values,
+        warps per CTA, CTAs per tile)."""
+        n = C.c_int32()
+        self._check(self.lib.ttn_tuning_get(self.h, None, 0, C.byref(n)), "ttn_tuning_get")
+        rows = np.zeros((n.value, _lib.TTN_TUNING_COLS), np.int32)
+        if n.value:
+            self._check(self.lib.ttn_tuning_get(self.h, ptr(rows, C.c_int32), n.value, C.byref(n)), "ttn_tuning_get")
+        return rows
+
+    def ttn_tuning_set(self, rows: np.ndarray) -> int:
+        """Give every list whose key matches a row that row's tile shape;
+        returns the number of lists set."""
+        r = np.ascontiguousarray(rows, dtype=np.int32).reshape(-1, _lib.TTN_TUNING_COLS)
+        n = C.c_int32()
+        self._check(self.lib.ttn_tuning_set(self.h, ptr(r, C.c_int32), len(r), C.byref(n)), "ttn_tuning_set")
+        return n.value
 
     def ttn_split_log(self):
         """(features [n, 24] float32, classes [n] int32) of the full-SVD ps2 splits so far."""
@@ -333,6 +387,20 @@ def ttn_batch_step(handles: Sequence["TTN"], dt: float, scheme: int = TTN_PS1, n
     if st != TTN_OK:
         msg = library().ttn_last_error(handles[0].h)
         raise TTNError(st, f"ttn_batch_step: {msg.decode() if msg else ''}")
+
+
+def ttn_batch_autotune(handles: Sequence["TTN"], dt: float, reps: int = 2) -> dict:
+    """Tile shape of a batch (C ABI ttn_batch_autotune): warps per CTA chosen by
+    timing the batched step; the members' states are put back afterwards.
+    Returns {"warps": w, "ms_per_batched_step": {8: .., 4: .., 2: ..}}."""
+    arr = (C.c_void_p * len(handles))(*[t.h for t in handles])
+    w = C.c_int32()
+    ms = (C.c_float * 3)()
+    st = library().ttn_batch_autotune(arr, len(handles), float(dt), int(reps), C.byref(w), ms)
+    if st != TTN_OK:
+        msg = library().ttn_last_error(handles[0].h)
+        raise TTNError(st, f"ttn_batch_autotune: {msg.decode() if msg else ''}")
+    return {"warps": int(w.value), "ms_per_batched_step": {8: float(ms[0]), 4: float(ms[1]), 2: float(ms[2])}}
 
 
 def pad_to_three_legs(parent: Sequence[int], leg_node: Sequence[int], leg_dims: Sequence[int]):

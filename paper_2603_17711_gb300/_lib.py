@@ -19,6 +19,7 @@ STATUS_NAMES = ["TTN_OK", "TTN_EINVAL", "TTN_ENOMEM", "TTN_ECUDA", "TTN_ENUMERIC
                 "TTN_ESTATE", "TTN_EUNSUPPORTED"]
 TTN_FP64, TTN_MIXED_FP32 = 0, 1
 TTN_PS1, TTN_PS2, TTN_VMF, TTN_MIX = 1, 2, 3, 4
+TTN_TUNING_COLS = 11  # int32 per row of ttn_tuning_get / ttn_tuning_set
 
 
 class ttn_tree(C.Structure):
@@ -30,7 +31,8 @@ class ttn_params(C.Structure):
     _fields_ = [("qr_tol", C.c_double), ("kappa", C.c_double), ("ps2_atol", C.c_double),
                 ("ps2_ratio", C.c_double), ("max_rank", C.c_int32), ("svd_tol", C.c_double),
                 ("max_split", C.c_int32), ("tensor_cores", C.c_int32), ("wait_s", C.c_double),
-                ("ode_rtol", C.c_double), ("ode_atol", C.c_double), ("vmf_atol", C.c_double)]
+                ("ode_rtol", C.c_double), ("ode_atol", C.c_double), ("vmf_atol", C.c_double),
+                ("tile_warps", C.c_int32)]
 
 
 DRIVE_FN = C.CFUNCTYPE(C.c_double, C.c_double, C.c_void_p)
@@ -69,6 +71,10 @@ SIGNATURES = [
     ("ttn_profile_read", C.c_int, [_h, C.c_int32, _f64p]),
     ("ttn_stats_reset", C.c_int, [_h]),
     ("ttn_autotune", C.c_int, [_h, C.c_int32]),
+    ("ttn_tuning_get", C.c_int, [_h, _i32p, C.c_int32, _i32p]),
+    ("ttn_tuning_set", C.c_int, [_h, _i32p, C.c_int32, _i32p]),
+    ("ttn_batch_autotune", C.c_int, [C.POINTER(_h), C.c_int32, C.c_double, C.c_int32, _i32p,
+                                     C.POINTER(C.c_float)]),
     ("ttn_svd_workspace_size", C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
     ("ttn_svd", C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, _f64p, C.c_void_p, C.c_void_p, C.c_size_t,
                           C.c_double, _i32p, C.c_void_p]),

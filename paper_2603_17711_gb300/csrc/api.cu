@@ -3,9 +3,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <exception>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -32,7 +34,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct ttn_ctx {
   Plan plan;
   int precision = TTN_FP64;
-  ttn_params params{1e-9, 2.5, 1e-7, 2.0, 32, 1e-12, kMaxSplit, 1, 2.0, 1e-5, 1e-7, 1e-10};
+  ttn_params params{1e-9, 2.5, 1e-7, 2.0, 32, 1e-12, kMaxSplit, 1, 2.0, 1e-5, 1e-7, 1e-10, 0};
   bool sop_loaded = false;
   bool ws_bound = false;
   bool envs_dirty = true;
@@ -1006,7 +1008,8 @@ ttn_status ttn_set_params(ttn_t h, const ttn_params* prm) {
     if (!(prm->qr_tol >= 0) || !(prm->kappa > 0) || !(prm->ps2_atol >= 0) || !(prm->ps2_ratio >= 1) ||
         prm->max_rank < 1 || !(prm->svd_tol >= 0) || prm->max_split < 1 || prm->max_split > kMaxSplit ||
         (prm->tensor_cores < 0 || prm->tensor_cores > 2) || !(prm->wait_s >= 0.0 && prm->wait_s <= 60.0) ||
-        !(prm->ode_rtol > 0.0) || !(prm->ode_atol > 0.0) || !(prm->vmf_atol >= 0.0))
+        !(prm->ode_rtol > 0.0) || !(prm->ode_atol > 0.0) || !(prm->vmf_atol >= 0.0) ||
+        !(prm->tile_warps == 0 || prm->tile_warps == 2 || prm->tile_warps == 4 || prm->tile_warps == 8))
       return h->fail(TTN_EINVAL, "parameter out of range");
     if (h->ws_bound && prm->max_rank != h->params.max_rank)
       return h->fail(TTN_ESTATE, "max_rank must be set before the workspace is bound");
@@ -1018,7 +1021,8 @@ ttn_status ttn_set_params(ttn_t h, const ttn_params* prm) {
         if (!e.empty()) return h->fail(TTN_EINVAL, e);
       }
     }
-    h->plan.set_split(prm->max_split);
+    if (prm->max_split != h->params.max_split || prm->tile_warps != h->params.tile_warps)
+      h->plan.set_split(prm->max_split, prm->tile_warps);
     h->params = *prm;
     h->drop_graph();  // substep counts, tolerances and launch shapes are baked into a captured step
     return TTN_OK;
@@ -1818,6 +1822,70 @@ ttn_status ttn_batch_step(ttn_t* hs, int32_t n, double dt, int32_t scheme, int32
   });
 }
 
+ttn_status ttn_batch_autotune(ttn_t* hs, int32_t n, double dt, int32_t reps, int32_t* warps_out, float* ms_out) {
+  if (!hs || n < 1 || reps < 1 || reps > 100) return TTN_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (!hs[i]) return TTN_EINVAL;
+  ttn_t h0 = hs[0];
+  return guarded(h0, [&]() -> ttn_status {
+    if (!(std::isfinite(dt)) || dt <= 0) return h0->fail(TTN_EINVAL, "bad dt");
+    // every member's state, to be put back after the timed steps
+    std::vector<std::vector<char>> saved(n);
+    for (int i = 0; i < n; ++i) {
+      size_t b = 0;
+      ttn_status st = ttn_checkpoint_size(hs[i], &b);
+      if (st == TTN_OK) {
+        saved[i].resize(b);
+        st = ttn_checkpoint_save(hs[i], saved[i].data(), b);
+      }
+      if (st != TTN_OK) return h0->fail(st, std::string("batch member: ") + hs[i]->err);
+    }
+    auto set_warps = [&](int w) -> ttn_status {
+      for (int i = 0; i < n; ++i) {
+        ttn_params q = hs[i]->params;
+        q.tile_warps = w;
+        ttn_status st = ttn_set_params(hs[i], &q);
+        if (st != TTN_OK) return h0->fail(st, std::string("batch member: ") + hs[i]->err);
+      }
+      return TTN_OK;
+    };
+    cudaEvent_t e0, e1;
+    CUDA_TRY(h0, cudaEventCreate(&e0));
+    CUDA_TRY(h0, cudaEventCreate(&e1));
+    const int cand[3] = {8, 4, 2};
+    int best = 8;
+    float tb = 3.4e38f;
+    ttn_status st = TTN_OK;
+    for (int c = 0; c < 3 && st == TTN_OK; ++c) {
+      st = set_warps(cand[c]);
+      if (st == TTN_OK) st = ttn_batch_step(hs, n, dt, TTN_PS1, 1);  // capture + warm-up
+      if (st != TTN_OK) break;
+      cudaEventRecord(e0, h0->stream);
+      st = ttn_batch_step(hs, n, dt, TTN_PS1, reps);
+      cudaEventRecord(e1, h0->stream);
+      if (st != TTN_OK || cudaEventSynchronize(e1) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms_out) ms_out[c] = ms / reps;
+      if (ms < 0.97f * tb) {  // the planned shape first: another must win by 3 %
+        tb = ms;
+        best = cand[c];
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != TTN_OK) return st;
+    CUDA_TRY(h0, cudaGetLastError());
+    st = set_warps(best);
+    for (int i = 0; i < n && st == TTN_OK; ++i) {
+      st = ttn_checkpoint_load(hs[i], saved[i].data(), saved[i].size());
+      if (st != TTN_OK) return h0->fail(st, std::string("batch member: ") + hs[i]->err);
+    }
+    if (warps_out) *warps_out = best;
+    return st;
+  });
+}
+
 ttn_status ttn_stats(ttn_t h, int32_t kind, int64_t* launches, double* flops) {
   if (!h || kind < 0 || kind > 4) return TTN_EINVAL;
   if (kind == 4) {
@@ -1844,6 +1912,27 @@ ttn_status ttn_profile_read(ttn_t h, int32_t kind, double* ms) {
   *ms = h->prof_ms[kind];
   return TTN_OK;
 }
+
+namespace {
+using TuneKey = std::array<int32_t, 9>;
+TuneKey ap_key(const Plan& p, const ApList& L, int prec) {
+  const ApOut& o = p.ap_outs[L.out_begin];
+  const int nt = p.ap_outs[L.out_end - 1].term_end - o.term_begin;
+  return {0, prec, o.d0, o.d1, o.d2, o.d3, L.out_end - L.out_begin, nt, L.n_tiles};
+}
+TuneKey pj_key(const Plan& p, const PjList& L, int prec) {
+  const PjOut& o = p.pj_outs[L.out_begin];
+  return {1, prec, o.d0, o.d1, o.d2, o.leg, L.out_end - L.out_begin, 0, L.n_tiles};
+}
+// precision each apply list runs in (absorb lists are FP64 in both forms)
+std::vector<int> ap_precs(const Plan& p, int prec) {
+  std::vector<int> pr(p.ap_lists.size(), prec);
+  for (const auto& a : p.absorb)
+    for (int id : a)
+      if (id >= 0) pr[id] = PREC_F64;
+  return pr;
+}
+}  // namespace
 
 ttn_status ttn_autotune(ttn_t h, int32_t reps) {
   return guarded(h, [&]() -> ttn_status {
@@ -1876,6 +1965,7 @@ ttn_status ttn_autotune(ttn_t h, int32_t reps) {
     const Epi rk1{EPI_RK1, h->h_bufs[p.buf.tmp], h->h_bufs_lo[p.buf.tmp], h->h_bufs_lo[p.buf.ys2],
                   h->h_bufs[p.buf.acc], 0.0};
     const int cap = std::min(kMaxSplit, h->params.max_split);
+    std::map<TuneKey, std::pair<int, int>> done;  // shape chosen per list key
     for (size_t i = 0; i < p.ap_lists.size(); ++i) {
       ApList& L = p.ap_lists[i];
       if (L.n_tiles <= 0) continue;
@@ -1885,32 +1975,52 @@ ttn_status ttn_autotune(ttn_t h, int32_t reps) {
           tc_applicable(L, p.ap_outs.data(), p.ap_terms.data()))
         continue;
       const bool epi = p.ap_outs[L.out_begin].dst < 0;
-      int best = 1;
-      float tb = 3.4e38f;
-      // splits only pay below a few CTAs per SM: larger lists keep one CTA per tile
-      const int kmax = std::max(1, std::min(std::min(L.useful, cap), 4 * p.sm_count / L.n_tiles));
-      if (kmax == 1) {
-        L.k = 1;
+      const TuneKey key = ap_key(p, L, prec);
+      auto seen = done.find(key);
+      if (seen != done.end()) {  // lists of one shape share one tuning
+        L.w = seen->second.first;
+        L.k = seen->second.second;
+        L.useful = (L.units + L.w - 1) / L.w;
         continue;
       }
-      for (int k = 1; k <= kmax; ++k) {
-        ApList L2 = L;
-        L2.k = k;
-        const float t = time_of([&] { launch_apply(prec, T, L2, epi ? rk1 : store, s); });
-        if (t < 0.97f * tb) {  // a larger split must win by 3 %
-          tb = t;
-          best = k;
+      int best_w = kSplitWarps, best_k = 1;
+      float tb = 3.4e38f;
+      for (int w : {8, 4, 2}) {  // the planned shape first: another must win by 3 %
+        const int useful = (L.units + w - 1) / w;
+        // splits only pay below a few CTAs per SM: larger lists keep one CTA per tile
+        const int kmax = std::max(1, std::min(std::min(useful, cap), (32 / w) * p.sm_count / L.n_tiles));
+        for (int k = 1; k <= kmax; ++k) {
+          ApList L2 = L;
+          L2.w = w;
+          L2.k = k;
+          L2.useful = useful;
+          const float t = time_of([&] { launch_apply(prec, T, L2, epi ? rk1 : store, s); });
+          if (t < 0.97f * tb) {
+            tb = t;
+            best_w = w;
+            best_k = k;
+          }
         }
       }
-      L.k = best;
+      L.w = best_w;
+      L.k = best_k;
+      L.useful = (L.units + best_w - 1) / best_w;
+      done.emplace(key, std::make_pair(best_w, best_k));
     }
     for (PjList& L : p.pj_lists) {
       if (L.n_tiles <= 0) continue;
+      const TuneKey key = pj_key(p, L, h->prec);
+      auto seen = done.find(key);
+      if (seen != done.end()) {
+        L.k = seen->second.second;
+        continue;
+      }
       int best = L.k;
       float tb = 3.4e38f;
       const int kmax = std::max(1, std::min(std::min(L.useful, cap), 4 * p.sm_count / L.n_tiles));
       if (kmax == 1) {
         L.k = 1;
+        done.emplace(key, std::make_pair(kSplitWarps, 1));
         continue;
       }
       for (int k = 1; k <= kmax; ++k) {
@@ -1923,11 +2033,75 @@ ttn_status ttn_autotune(ttn_t h, int32_t reps) {
         }
       }
       L.k = best;
+      done.emplace(key, std::make_pair(kSplitWarps, best));
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CUDA_TRY(h, cudaGetLastError());
     h->envs_dirty = true;
+    h->drop_graph();
+    return TTN_OK;
+  });
+}
+
+
+ttn_status ttn_tuning_get(ttn_t h, int32_t* rows, int32_t max_rows, int32_t* n_rows) {
+  if (!h || !n_rows || max_rows < 0 || (max_rows > 0 && !rows)) return TTN_EINVAL;
+  return guarded(h, [&]() -> ttn_status {
+    if (!h->sop_loaded) return h->fail(TTN_ESTATE, "sop_load first");
+    const Plan& p = h->plan;
+    const std::vector<int> pr = ap_precs(p, h->prec);
+    int n = 0;
+    auto put = [&](const TuneKey& k, int w, int kk) {
+      if (n < max_rows) {
+        int32_t* r = rows + (size_t)n * TTN_TUNING_COLS;
+        for (int i = 0; i < 9; ++i) r[i] = k[i];
+        r[9] = w;
+        r[10] = kk;
+      }
+      ++n;
+    };
+    for (size_t i = 0; i < p.ap_lists.size(); ++i) put(ap_key(p, p.ap_lists[i], pr[i]), p.ap_lists[i].w, p.ap_lists[i].k);
+    for (const PjList& L : p.pj_lists) put(pj_key(p, L, h->prec), kSplitWarps, L.k);
+    *n_rows = n;
+    return TTN_OK;
+  });
+}
+
+ttn_status ttn_tuning_set(ttn_t h, const int32_t* rows, int32_t n_rows, int32_t* n_applied) {
+  if (!h || n_rows < 0 || (n_rows > 0 && !rows)) return TTN_EINVAL;
+  return guarded(h, [&]() -> ttn_status {
+    if (!h->sop_loaded) return h->fail(TTN_ESTATE, "sop_load first");
+    const int cap = std::min(kMaxSplit, h->params.max_split);
+    std::map<TuneKey, std::pair<int, int>> shape;
+    for (int i = 0; i < n_rows; ++i) {
+      const int32_t* r = rows + (size_t)i * TTN_TUNING_COLS;
+      const int w = r[9], k = r[10];
+      const bool w_ok = r[0] == 0 ? (w == 2 || w == 4 || w == 8) : (r[0] == 1 && w == kSplitWarps);
+      if (!w_ok || k < 1 || k > cap) return h->fail(TTN_EINVAL, "tuning row " + std::to_string(i) + " out of range");
+      TuneKey key;
+      for (int j = 0; j < 9; ++j) key[j] = r[j];
+      shape.emplace(key, std::make_pair(w, k));  // the first row of a key wins
+    }
+    Plan& p = h->plan;
+    const std::vector<int> pr = ap_precs(p, h->prec);
+    int applied = 0;
+    for (size_t i = 0; i < p.ap_lists.size(); ++i) {
+      ApList& L = p.ap_lists[i];
+      auto it = shape.find(ap_key(p, L, pr[i]));
+      if (it == shape.end()) continue;
+      L.w = it->second.first;
+      L.k = it->second.second;
+      L.useful = (L.units + L.w - 1) / L.w;
+      ++applied;
+    }
+    for (PjList& L : p.pj_lists) {
+      auto it = shape.find(pj_key(p, L, h->prec));
+      if (it == shape.end()) continue;
+      L.k = it->second.second;
+      ++applied;
+    }
+    if (n_applied) *n_applied = applied;
     h->drop_graph();
     return TTN_OK;
   });

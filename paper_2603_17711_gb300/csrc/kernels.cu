@@ -71,15 +71,17 @@ template <> struct Cx<float> {
 // Sum of mode products: out_o[idx] = sum_t M_t x_{leg_t} src_t.
 // An output tile is 32 consecutive elements (one per lane). Its work is cut
 // into units -- an identity term, or kApChunk consecutive positions x of one
-// mode product -- dealt round-robin to the 8*k warps of the k CTAs (one
+// mode product -- dealt round-robin to the NW*k warps of the k CTAs (one
 // thread-block cluster) that share the tile. Each warp sums its units in
 // order, the CTA sums its warps in order, and CTA 0 of the cluster sums the
 // CTAs in order (through distributed shared memory), so results are bitwise
-// reproducible. GB300 issues one FP64 instruction per warp every ~64 cycles,
-// so short dependency chains (8 positions per unit, loads issued before the
-// FMAs) and many warps per tile are what makes a small contraction fast.
+// reproducible for a given tile shape (NW, k). GB300 issues one FP64
+// instruction per warp every ~64 cycles, so short dependency chains (4
+// positions per unit, loads issued before the FMAs) and many warps per tile
+// make a small contraction fast; when many lists run at once (batched
+// instances) fewer warps per tile waste less on idle warps and reductions.
+// NW (warps per CTA: 2, 4 or 8) and k are chosen per list (ApList::w, k).
 // ---------------------------------------------------------------------------
-constexpr int kApWarps = kSplitWarps;
 
 // Leg geometry of one output element (kept in registers: selected by switch,
 // never indexed dynamically).
@@ -136,7 +138,7 @@ __device__ __forceinline__ typename Cx<R>::T unit_dot(const ApTerm& term, const 
 
 // Sum of one output tile over the units of CTA `rank` of the k sharing it;
 // the CTA's total (fixed order over warps) is returned in warp 0.
-template <typename R>
+template <typename R, int NW>
 __device__ __forceinline__ typename Cx<R>::T tile_sum(const DevTables& T, const ApList& L, int tile, int rank, int K,
                                                       typename Cx<R>::T (*part)[32], ApOut& out, int64_t& idx,
                                                       int64_t& P) {
@@ -159,7 +161,7 @@ __device__ __forceinline__ typename Cx<R>::T tile_sum(const DevTables& T, const 
     g.i1 = (int)((idx / g.s1) % g.d1);
     g.i2 = (int)((idx / g.s2) % g.d2);
     g.i3 = (int)(idx % g.d3);
-    const int W = K * kApWarps, me = rank * kApWarps + wid;
+    const int W = K * NW, me = rank * NW + wid;
     int u = 0;  // index of the term's first unit in the tile's unit list
     for (int t = out.term_begin; t < out.term_end; ++t) {
       const ApTerm term = T.terms[t];
@@ -173,7 +175,7 @@ __device__ __forceinline__ typename Cx<R>::T tile_sum(const DevTables& T, const 
   __syncthreads();
   if (wid == 0) {
     acc = part[0][lane];
-    for (int w = 1; w < kApWarps; ++w) acc = C::add(acc, part[w][lane]);
+    for (int w = 1; w < NW; ++w) acc = C::add(acc, part[w][lane]);
   }
   __syncthreads();  // part may be reused by the caller's next tile
   return acc;
@@ -216,18 +218,18 @@ __device__ __forceinline__ void tile_store(const DevTables& T, const ApOut& out,
   }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(32 * kApWarps, 4) k_apply(DevTables T, ApList L, Epi ep) {
+template <typename R, int NW>
+__global__ void __launch_bounds__(32 * NW, 32 / NW) k_apply(DevTables T, ApList L, Epi ep) {
   using C = Cx<R>;
   using V = typename C::T;
-  __shared__ V part[kApWarps][32];
+  __shared__ V part[NW][32];
   __shared__ V slot[kMaxSplit][32];
   const int K = L.k;
   const int tile = blockIdx.x / K, rank = blockIdx.x % K;  // rank == block rank in the cluster
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   ApOut out;
   int64_t idx, P;
-  V acc = tile_sum<R>(T, L, tile, rank, K, part, out, idx, P);
+  V acc = tile_sum<R, NW>(T, L, tile, rank, K, part, out, idx, P);
   if (K > 1) {
     cg::cluster_group cluster = cg::this_cluster();
     if (wid == 0 && rank > 0) cluster.map_shared_rank(&slot[0][0], 0)[rank * 32 + lane] = acc;
@@ -242,14 +244,14 @@ __global__ void __launch_bounds__(32 * kApWarps, 4) k_apply(DevTables T, ApList 
 
 // Launch n_tiles * k CTAs; k > 1 makes every k consecutive CTAs one cluster.
 template <typename Kern, typename... Args>
-static void launch_split(Kern kern, int n_tiles, int k, cudaStream_t s, Args... args) {
+static void launch_split(Kern kern, int n_tiles, int k, int warps, cudaStream_t s, Args... args) {
   if (k <= 1) {
-    kern<<<n_tiles, 32 * kSplitWarps, 0, s>>>(args...);
+    kern<<<n_tiles, 32 * warps, 0, s>>>(args...);
     return;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_tiles * k), 1, 1);
-  cfg.blockDim = dim3(32 * kSplitWarps, 1, 1);
+  cfg.blockDim = dim3(32 * warps, 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -262,12 +264,21 @@ static void launch_split(Kern kern, int n_tiles, int k, cudaStream_t s, Args... 
   cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+template <typename R>
+static void launch_apply_w(const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s) {
+  switch (L.w) {
+    case 2: launch_split(k_apply<R, 2>, L.n_tiles, L.k, 2, s, T, L, e); break;
+    case 4: launch_split(k_apply<R, 4>, L.n_tiles, L.k, 4, s, T, L, e); break;
+    default: launch_split(k_apply<R, 8>, L.n_tiles, L.k, 8, s, T, L, e); break;
+  }
+}
+
 void launch_apply(int prec, const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s) {
   if (L.n_tiles <= 0) return;
   if (prec == PREC_F32)
-    launch_split(k_apply<float>, L.n_tiles, L.k, s, T, L, e);
+    launch_apply_w<float>(T, L, e, s);
   else
-    launch_split(k_apply<double>, L.n_tiles, L.k, s, T, L, e);
+    launch_apply_w<double>(T, L, e, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -462,9 +473,9 @@ bool launch_project_tiled(int prec, const DevTables& T, const PjList& L, int d, 
 void launch_project(int prec, const DevTables& T, const PjList& L, cudaStream_t s) {
   if (L.n_tiles <= 0) return;
   if (prec == PREC_F32)
-    launch_split(k_project<float>, L.n_tiles, L.k, s, T, L);
+    launch_split(k_project<float>, L.n_tiles, L.k, kPjWarps, s, T, L);
   else
-    launch_split(k_project<double>, L.n_tiles, L.k, s, T, L);
+    launch_split(k_project<double>, L.n_tiles, L.k, kPjWarps, s, T, L);
 }
 
 // ---------------------------------------------------------------------------

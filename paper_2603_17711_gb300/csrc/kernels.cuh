@@ -181,12 +181,59 @@ __host__ __device__ inline double jacobi_negligible(int rows, double fro2) {
   return 16.0 * rows * 2.220446049250313e-16 * 2.220446049250313e-16 * fro2;
 }
 constexpr int kJacMaxSweeps = 60;
-// The same SVD over the whole GPU (svd.cu): pairs of a circle-method round dealt
-// to the CTAs of one cooperative launch, one grid barrier per round. Used when
-// the smaller side has at least kJacGridMinCols columns (else the one-CTA
-// kernel). sync: kSvdSyncInts device ints (cleared by the launch); a grid wait
-// longer than wait_ns sets bit 4 (16) of *flag. Same outputs as launch_jacobi_svd.
-constexpr int kJacGridMinCols = 24;
+
+// Rotation of one column pair of the one-sided Jacobi SVD from its Gram
+// entries a = |x|^2, b = |y|^2 and c = x^H y = cr + i ci. Returns false when
+// the pair is left alone: |c|^2 <= tol^2 a b (orthogonal to working accuracy),
+// c = 0, or a column is rounding noise (min(a, b) <= tiny2, jacobi_negligible).
+// Otherwise the complex rotation
+//     x' = cs x - sn e y,   y' = sn x + cs e y,   e = conj(c) / |c|
+// makes the pair orthogonal; t = sn / cs is the root of smaller modulus of
+// t^2 + 2 zeta t - 1 = 0, zeta = (b - a) / (2 |c|), written without zeta:
+//     t = sign(b - a) 2|c| / (|b - a| + sqrt((b - a)^2 + 4 |c|^2)),
+//     cs = 1 / sqrt(1 + t^2),   sn = t cs.
+// Both square roots are independent, then both quotients (t and 1/|c|), so
+// the dependent chain is square root, quotient, reciprocal square root.
+__device__ __forceinline__ bool jacobi_rotation(double a, double b, double cr, double ci, double tol, double tiny2,
+                                                double& cs, double& sn, double2& e) {
+  const double c2 = cr * cr + ci * ci;
+  if (!(c2 > tol * tol * a * b) || c2 == 0.0 || !(fmin(a, b) > tiny2)) return false;
+  const double d = b - a;
+  const double s1 = sqrt(c2);
+  const double s2 = sqrt(fma(d, d, 4.0 * c2));
+  const double t = (d >= 0.0 ? 2.0 * s1 : -2.0 * s1) / (fabs(d) + s2);
+  const double inv = 1.0 / s1;
+  cs = rsqrt(fma(t, t, 1.0));
+  sn = t * cs;
+  e = make_double2(cr * inv, -ci * inv);
+  return true;
+}
+
+// Sums of four per-lane values over a warp in a fixed order (reduce-scatter:
+// 6 additions instead of 20). On return lanes 0-7 hold the sum of v0, lanes
+// 8-15 of v1, lanes 16-23 of v2 and lanes 24-31 of v3.
+__device__ __forceinline__ double warp_sum4(double v0, double v1, double v2, double v3) {
+  const int lane = threadIdx.x & 31;
+  const bool hi = (lane & 16) != 0;
+  double k0 = hi ? v2 : v0, k1 = hi ? v3 : v1;
+  const double s0 = hi ? v0 : v2, s1 = hi ? v1 : v3;
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+  const bool h8 = (lane & 8) != 0;
+  double k = h8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+  for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  return k;
+}
+// The same SVD spread over several CTAs (svd.cu): pairs of a circle-method
+// round dealt to the CTAs, one barrier per round -- the hardware barrier of
+// one thread-block cluster for up to 2 * kJacClusterMax columns, else a grid
+// barrier of one cooperative launch. Used when the smaller side has more than
+// kJacOneCtaMaxCols columns (else the one-CTA kernel). sync: kSvdSyncInts device
+// ints (cleared by the launch); a grid wait longer than wait_ns sets bit 4 (16)
+// of *flag. Same outputs as launch_jacobi_svd.
+constexpr int kJacOneCtaMaxCols = 16;
+constexpr int kJacClusterMax = 16;
 constexpr int kSvdSyncInts = 128;
 bool launch_jacobi_svd_grid(const double2* theta, int m, int n, double2* A, double2* V, double* sigma, int* info,
                             unsigned* sync, int* flag, uint64_t wait_ns, cudaStream_t s);

@@ -493,9 +493,15 @@ int Plan::split_factor(int tiles, int useful) const {
   return k;
 }
 
-void Plan::set_split(int m) {
+void Plan::set_split(int m, int tw) {
   max_split = m;
-  for (ApList& L : ap_lists) L.k = split_factor(L.n_tiles, L.useful);
+  tile_warps = tw;
+  const int w = tw > 0 ? tw : kSplitWarps;
+  for (ApList& L : ap_lists) {
+    L.w = w;
+    L.useful = (L.units + w - 1) / w;
+    L.k = split_factor(L.n_tiles, L.useful);
+  }
   for (PjList& L : pj_lists) L.k = split_factor(L.n_tiles, L.useful);
 }
 
@@ -531,7 +537,9 @@ int Plan::add_list(const std::vector<ApOut>& outs, const std::vector<std::vector
     for (const ApTerm& t : tl[i]) u += t.mat < 0 ? 1 : (dd[t.leg] + kApChunk - 1) / kApChunk;
     units_max = std::max(units_max, u);
   }
-  L.useful = (units_max + kSplitWarps - 1) / kSplitWarps;
+  L.units = units_max;
+  L.w = tile_warps > 0 ? tile_warps : kSplitWarps;
+  L.useful = (units_max + L.w - 1) / L.w;
   L.k = split_factor(tiles, L.useful);
   ap_lists.push_back(L);
   return (int)ap_lists.size() - 1;

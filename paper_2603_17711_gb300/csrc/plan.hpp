@@ -106,7 +106,9 @@ struct ApList {
   int32_t out_begin, out_end;  // into the global ApOut table
   int32_t n_tiles;
   int32_t k = 1;       // CTAs sharing one output tile (thread-block cluster size, 1..8)
-  int32_t useful = 1;  // largest split that still gives every warp work
+  int32_t useful = 1;  // largest split that still gives every warp work (for w warps per CTA)
+  int32_t w = 8;       // warps per CTA (2, 4 or 8): with k, the tile shape of the launch
+  int32_t units = 1;   // work units of the list's largest output tile
   double flops;        // algorithmic: 8 * P * d_leg per non-identity term and output
 };
 // Projection job: E[x',x] = sum_r conj(U[.. x' at leg ..]) W[.. x at leg ..].
@@ -179,6 +181,7 @@ struct Plan {
   int cap_rank = 32;
   int sm_count = 152;  // SMs of the device: sizes the per-tile CTA split of the job lists
   int max_split = 8;   // upper bound of that split (ttn_params.max_split)
+  int tile_warps = 0;  // warps per CTA of new apply lists (ttn_params.tile_warps; 0: kSplitWarps)
 
   // classes
   std::vector<std::vector<ClassId>> dir_classes;  // per directed bond id
@@ -225,7 +228,9 @@ struct Plan {
   int n_sub(double tau, double kappa) const;
   bool built_jobs = false;
   std::string build_jobs();
-  void set_split(int max_split);  // recompute the split of every job list
+  // recompute the tile shape of every job list: tile_warps warps per CTA of the
+  // apply lists (0: kSplitWarps) and the planned split below max_split
+  void set_split(int max_split, int tw = 0);
 
  private:
   std::string build_classes();

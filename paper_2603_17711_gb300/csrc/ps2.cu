@@ -69,10 +69,19 @@ void launch_merge(const double2* Uf, const int* fd, int lf, const double2* Us, c
 }
 
 constexpr int kJacThreads = 512;
+constexpr int kJacChunk = 128;  // pairs of one round whose Gram entries and rotations sit in shared memory
 
+// One round of pairs is handled in three phases, chunk by chunk: each warp sums
+// the Gram entries of its pairs (lanes split the rows), one lane per pair then
+// computes the rotations of the whole chunk (so the square roots and quotients
+// cost one warp instruction stream instead of one per pair), and the warps
+// apply them to their pairs' columns of A and V.
 __global__ void __launch_bounds__(kJacThreads) k_jacobi(const double2* theta, int m, int n, double2* A, double2* V,
                                                         double* sigma, int* info, double tol, int max_sweeps) {
   __shared__ int s_rot;
+  __shared__ double s_g[kJacChunk][4];
+  __shared__ double s_r[kJacChunk][4];
+  __shared__ int s_go[kJacChunk];
   const bool tr = n > m;
   const int nr = tr ? n : m, nc = tr ? m : n;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -96,62 +105,83 @@ __global__ void __launch_bounds__(kJacThreads) k_jacobi(const double2* theta, in
   double fro2 = 0.0;
   for (int w = 0; w < nw; ++w) fro2 += s_fro[w];
   const double tiny2 = jacobi_negligible(nr, fro2);
-  const int N = nc + (nc & 1);
+  const int N = nc + (nc & 1), npairs = N / 2;
+  auto pair_of = [&](int rd, int p, int& i, int& j) {
+    if (p == 0) {
+      i = 0;
+      j = 1 + rd;
+    } else {
+      i = 1 + (rd + p) % (N - 1);
+      j = 1 + (rd - p + N - 1) % (N - 1);
+    }
+    if (i > j) {
+      const int t = i;
+      i = j;
+      j = t;
+    }
+  };
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int rd = 0; rd < N - 1; ++rd) {
-      for (int p = wid; p < N / 2; p += nw) {
-        int i, j;
-        if (p == 0) {
-          i = 0;
-          j = 1 + rd;
-        } else {
-          i = 1 + (rd + p) % (N - 1);
-          j = 1 + (rd - p + N - 1) % (N - 1);
+      for (int p0 = 0; p0 < npairs; p0 += kJacChunk) {
+        const int np = min(kJacChunk, npairs - p0);
+        for (int q = wid; q < np; q += nw) {  // Gram entries
+          int i, j;
+          pair_of(rd, p0 + q, i, j);
+          if (j >= nc) continue;
+          const double2* x = A + (int64_t)i * nr;
+          const double2* y = A + (int64_t)j * nr;
+          double a = 0.0, b = 0.0, cr = 0.0, ci = 0.0;
+          for (int r = lane; r < nr; r += 32) {
+            const double2 xv = x[r], yv = y[r];
+            a += xv.x * xv.x + xv.y * xv.y;
+            b += yv.x * yv.x + yv.y * yv.y;
+            cr += xv.x * yv.x + xv.y * yv.y;  // conj(x) y
+            ci += xv.x * yv.y - xv.y * yv.x;
+          }
+          const double sum = warp_sum4(a, b, cr, ci);
+          if ((lane & 7) == 0) s_g[q][lane >> 3] = sum;
         }
-        if (i > j) {
-          const int t = i;
-          i = j;
-          j = t;
+        __syncthreads();
+        for (int q = tid; q < np; q += blockDim.x) {  // rotations, one lane per pair
+          int i, j;
+          pair_of(rd, p0 + q, i, j);
+          double cs = 1.0, sn = 0.0;
+          double2 e = make_double2(1.0, 0.0);
+          const int go = j < nc && jacobi_rotation(s_g[q][0], s_g[q][1], s_g[q][2], s_g[q][3], tol, tiny2, cs, sn, e);
+          s_r[q][0] = cs;
+          s_r[q][1] = sn;
+          s_r[q][2] = e.x;
+          s_r[q][3] = e.y;
+          s_go[q] = go;
+          if (go) atomicAdd(&s_rot, 1);
         }
-        if (j >= nc) continue;
-        double2* x = A + (int64_t)i * nr;
-        double2* y = A + (int64_t)j * nr;
-        double a = 0.0, b = 0.0, cr = 0.0, ci = 0.0;
-        for (int r = lane; r < nr; r += 32) {
-          const double2 xv = x[r], yv = y[r];
-          a += xv.x * xv.x + xv.y * xv.y;
-          b += yv.x * yv.x + yv.y * yv.y;
-          cr += xv.x * yv.x + xv.y * yv.y;  // conj(x) y
-          ci += xv.x * yv.y - xv.y * yv.x;
+        __syncthreads();
+        for (int q = wid; q < np; q += nw) {  // apply
+          if (!s_go[q]) continue;
+          int i, j;
+          pair_of(rd, p0 + q, i, j);
+          const double cs = s_r[q][0], sn = s_r[q][1];
+          const double2 e = make_double2(s_r[q][2], s_r[q][3]);
+          double2* x = A + (int64_t)i * nr;
+          double2* y = A + (int64_t)j * nr;
+          for (int r = lane; r < nr; r += 32) {
+            const double2 xv = x[r], yv = cm(e, y[r]);
+            x[r] = make_double2(cs * xv.x - sn * yv.x, cs * xv.y - sn * yv.y);
+            y[r] = make_double2(sn * xv.x + cs * yv.x, sn * xv.y + cs * yv.y);
+          }
+          double2* vx = V + (int64_t)i * nc;
+          double2* vy = V + (int64_t)j * nc;
+          for (int r = lane; r < nc; r += 32) {
+            const double2 xv = vx[r], yv = cm(e, vy[r]);
+            vx[r] = make_double2(cs * xv.x - sn * yv.x, cs * xv.y - sn * yv.y);
+            vy[r] = make_double2(sn * xv.x + cs * yv.x, sn * xv.y + cs * yv.y);
+          }
         }
-        a = ws(a);
-        b = ws(b);
-        cr = ws(cr);
-        ci = ws(ci);
-        const double ac = sqrt(cr * cr + ci * ci);
-        if (!(ac > tol * sqrt(a * b)) || ac == 0.0 || !(fmin(a, b) > tiny2)) continue;
-        const double zeta = (b - a) / (2.0 * ac);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
-        const double2 e = make_double2(cr / ac, -ci / ac);  // exp(-i arg c)
-        for (int r = lane; r < nr; r += 32) {
-          const double2 xv = x[r], yv = cm(e, y[r]);
-          x[r] = make_double2(cs * xv.x - sn * yv.x, cs * xv.y - sn * yv.y);
-          y[r] = make_double2(sn * xv.x + cs * yv.x, sn * xv.y + cs * yv.y);
-        }
-        double2* vx = V + (int64_t)i * nc;
-        double2* vy = V + (int64_t)j * nc;
-        for (int r = lane; r < nc; r += 32) {
-          const double2 xv = vx[r], yv = cm(e, vy[r]);
-          vx[r] = make_double2(cs * xv.x - sn * yv.x, cs * xv.y - sn * yv.y);
-          vy[r] = make_double2(sn * xv.x + cs * yv.x, sn * xv.y + cs * yv.y);
-        }
-        if (lane == 0) atomicAdd(&s_rot, 1);
+        __syncthreads();
       }
-      __syncthreads();
     }
     const int rot = s_rot;
     __syncthreads();

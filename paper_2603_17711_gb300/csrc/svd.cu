@@ -1,24 +1,25 @@
-// One-sided (Hestenes) Jacobi SVD over the whole GPU, FP64 -- the factorisation
-// that splits a merged pair in the adaptive-rank scheme (Sec. 2.3, last
-// paragraph), for matrices too wide for one CTA.
+// One-sided (Hestenes) Jacobi SVD spread over several CTAs, FP64 -- the
+// factorisation that splits a merged pair in the adaptive-rank scheme (Sec. 2.3,
+// last paragraph), for matrices too wide for one CTA.
 //
 // The working matrix holds the columns of Theta (or of Theta^H when Theta is
 // wider than tall), column-major; V starts as the identity. A sweep visits every
 // column pair once, in the rounds of the circle method: the pairs of one round
-// are disjoint, so they are dealt to the CTAs of one cooperative launch and the
-// round ends with one grid barrier. A pair is handled by one CTA: its threads
-// split the rows, the three Gram entries a = |x|^2, b = |y|^2, c = x^H y are
-// summed in a fixed order (threads -> warps -> warp order), every thread then
-// holds the same sums and applies the same complex rotation
-//     x' = cs x - sn e y,  y' = sn x + cs e y,   e = conj(c)/|c|,
-//     zeta = (b - a) / (2|c|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
-//     cs = 1/sqrt(1 + t^2), sn = t cs,
-// to the pair's rows of the working matrix and of V, when |c| > tol sqrt(a b)
-// and neither column is rounding noise (squared norm above
-// 16 rows eps^2 ||A||_F^2, jacobi_negligible).
+// are disjoint, so they are dealt to the CTAs and the round ends with one
+// barrier -- the hardware barrier of a thread-block cluster when the pairs fit
+// one cluster (at most 16 CTAs), else a grid barrier of one cooperative launch.
+// A pair is handled by one CTA: its threads split the rows, the three Gram
+// entries a = |x|^2, b = |y|^2, c = x^H y are summed in a fixed order (threads
+// -> warps -> warp order), thread 0 computes the complex rotation
+// (jacobi_rotation: skipped when |c| <= tol sqrt(a b) or a column is rounding
+// noise) and the threads apply it to the pair's rows of the working matrix and
+// of V. GB300 retires about one FP64 warp instruction per 19 cycles per SM, and
+// a square root or quotient is a dozen of them: computing the rotation in one
+// thread instead of all eight warps keeps the FP64 pipe for the rows.
 // A sweep without any rotation ends the iteration: every CTA reads the sweep's
-// rotation count after the sweep's last barrier. Which CTA handles a pair does
-// not change its arithmetic, so the result does not depend on the grid size.
+// rotation count after the sweep's last barrier. Which CTA handles a pair, and
+// which barrier ends a round, does not change the arithmetic, so the result
+// does not depend on the launch shape.
 //
 // The convergence threshold tol = 2 sqrt(max(rows, 64)) * DBL_EPSILON sits above
 // the rounding noise of the Gram entries summed over the rows, so a converged
@@ -28,7 +29,9 @@
 // Every grid wait is bounded (wait_ns from the moment the CTA starts waiting);
 // a CTA whose wait gives up sets bit 4 (value 16) of *flag and returns. Nothing
 // is in flight when it does (plain loads and stores only), so any CTA may leave
-// at any time; the others give up at their next barrier.
+// at any time; the others give up at their next barrier. The cluster barrier is
+// the hardware's: all CTAs of a cluster are resident together and every CTA
+// passes the same number of barriers.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -36,8 +39,12 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "../../include/ttn_heom.h"
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ttn {
 
@@ -45,6 +52,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kRegRows = 4;  // rows of a pair's columns a thread keeps in registers (nr <= 1024 entirely)
+constexpr int kRegV = 2;     // rows of the pair's V columns a thread keeps in registers (nc <= 512 entirely)
+static_assert(kWarps * 4 == 32, "warp 0 adds four sums of each of the eight warps, one per lane");
 constexpr int kBarLanes = 8;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -133,13 +143,29 @@ __global__ void k_svd_load(const double2* __restrict__ theta, int m, int n, doub
   }
 }
 
+// Barrier at the end of a phase: the hardware barrier of the cluster (release /
+// acquire at cluster scope, which orders the global-memory writes of A and V
+// too), or the grid barrier of a cooperative launch.
+template <bool kCluster>
+__device__ __forceinline__ bool phase_sync(unsigned* lanes, unsigned target, uint64_t wait_ns, int* flag) {
+  if constexpr (kCluster) {
+    cg::this_cluster().sync();
+    return true;
+  } else {
+    return grid_sync(lanes, target, wait_ns, flag);
+  }
+}
+
 // sync: [0, 8) barrier lanes, [8, 8 + max_sweeps) rotations per sweep; zeroed
-// before the launch.
+// before the launch. kCluster: the CTAs form one thread-block cluster.
+template <bool kCluster>
 __global__ void __launch_bounds__(kThreads) k_jacobi_grid(double2* __restrict__ A, double2* __restrict__ V, int nr,
                                                           int nc, double* __restrict__ sigma, int* __restrict__ info,
                                                           unsigned* sync, int* flag, double tol, int max_sweeps,
                                                           int tr, uint64_t wait_ns) {
   __shared__ double s_red[kWarps][4];
+  __shared__ double s_par[4];
+  __shared__ int s_go;
   __shared__ unsigned s_total;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int G = gridDim.x;
@@ -163,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_grid(double2* __restrict__ 
     __syncthreads();
   }
   ++nbar;
-  ok = grid_sync(sync, nbar * (unsigned)G, wait_ns, flag);
+  ok = phase_sync<kCluster>(sync, nbar * (unsigned)G, wait_ns, flag);
   if (!ok) return;
   double fro2 = 0.0;
   for (int jc = 0; jc < nc; ++jc) fro2 += sigma[jc];
@@ -178,47 +204,93 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_grid(double2* __restrict__ 
         if (j >= nc) continue;  // the dummy column of an odd count
         double2* x = A + (int64_t)i * nr;
         double2* y = A + (int64_t)j * nr;
+        double2* vx = V + (int64_t)i * nc;
+        double2* vy = V + (int64_t)j * nc;
+        // the pair's first kRegRows rows per thread of x, y and of the V columns
+        // stay in registers from the Gram sums to the update; the V loads are
+        // issued first so that their latency hides behind the sums
+        double2 xr[kRegRows], yr[kRegRows], vxr[kRegV], vyr[kRegV];
+#pragma unroll
+        for (int q = 0; q < kRegV; ++q) {
+          const int r = tid + q * kThreads;
+          if (r < nc) {
+            vxr[q] = vx[r];
+            vyr[q] = vy[r];
+          }
+        }
         double a = 0.0, b = 0.0, cr = 0.0, ci = 0.0;
-        for (int r = tid; r < nr; r += kThreads) {
+#pragma unroll
+        for (int q = 0; q < kRegRows; ++q) {
+          const int r = tid + q * kThreads;
+          if (r < nr) {
+            xr[q] = x[r];
+            yr[q] = y[r];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kRegRows; ++q) {
+          if (tid + q * kThreads < nr) {
+            const double2 xv = xr[q], yv = yr[q];
+            a = fma(xv.x, xv.x, fma(xv.y, xv.y, a));
+            b = fma(yv.x, yv.x, fma(yv.y, yv.y, b));
+            cr = fma(xv.x, yv.x, fma(xv.y, yv.y, cr));  // Re conj(x) y
+            ci = fma(xv.x, yv.y, fma(-xv.y, yv.x, ci));  // Im conj(x) y
+          }
+        }
+        for (int r = tid + kRegRows * kThreads; r < nr; r += kThreads) {
           const double2 xv = x[r], yv = y[r];
           a = fma(xv.x, xv.x, fma(xv.y, xv.y, a));
           b = fma(yv.x, yv.x, fma(yv.y, yv.y, b));
-          cr = fma(xv.x, yv.x, fma(xv.y, yv.y, cr));  // Re conj(x) y
-          ci = fma(xv.x, yv.y, fma(-xv.y, yv.x, ci));  // Im conj(x) y
+          cr = fma(xv.x, yv.x, fma(xv.y, yv.y, cr));
+          ci = fma(xv.x, yv.y, fma(-xv.y, yv.x, ci));
         }
-        a = wsum(a);
-        b = wsum(b);
-        cr = wsum(cr);
-        ci = wsum(ci);
-        if (lane == 0) {
-          s_red[wid][0] = a;
-          s_red[wid][1] = b;
-          s_red[wid][2] = cr;
-          s_red[wid][3] = ci;
-        }
+        const double sum = warp_sum4(a, b, cr, ci);
+        if ((lane & 7) == 0) s_red[wid][lane >> 3] = sum;
         __syncthreads();
-        a = b = cr = ci = 0.0;
-        for (int w = 0; w < kWarps; ++w) {
-          a += s_red[w][0];
-          b += s_red[w][1];
-          cr += s_red[w][2];
-          ci += s_red[w][3];
+        if (wid == 0) {  // the rotation, once per pair: warp 0 adds the warps' sums, lane 0 rotates
+          // lane l holds quantity l & 3 of warp l >> 2; a fixed butterfly over the warp bits
+          double v = s_red[lane >> 2][lane & 3];
+          for (int o = 4; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          const double ga = __shfl_sync(0xffffffffu, v, 0), gb = __shfl_sync(0xffffffffu, v, 1);
+          const double gr = __shfl_sync(0xffffffffu, v, 2), gi = __shfl_sync(0xffffffffu, v, 3);
+          if (lane == 0) {
+            double cs, sn;
+            double2 e;
+            s_go = jacobi_rotation(ga, gb, gr, gi, tol, tiny2, cs, sn, e) ? 1 : 0;
+            s_par[0] = cs;
+            s_par[1] = sn;
+            s_par[2] = e.x;
+            s_par[3] = e.y;
+          }
         }
-        __syncthreads();  // s_red is rewritten by the next pair
-        const double ac = sqrt(cr * cr + ci * ci);
-        if (!(ac > tol * sqrt(a * b)) || ac == 0.0 || !(fmin(a, b) > tiny2)) continue;
-        const double zeta = (b - a) / (2.0 * ac);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
-        const double2 e = make_double2(cr / ac, -ci / ac);
-        for (int r = tid; r < nr; r += kThreads) {
+        __syncthreads();  // s_red and s_par are rewritten only after the next pair's sums
+        if (!s_go) continue;
+        const double cs = s_par[0], sn = s_par[1];
+        const double2 e = make_double2(s_par[2], s_par[3]);
+#pragma unroll
+        for (int q = 0; q < kRegRows; ++q) {
+          const int r = tid + q * kThreads;
+          if (r < nr) {
+            const double2 xv = xr[q], yv = cmul(e, yr[q]);
+            x[r] = make_double2(cs * xv.x - sn * yv.x, cs * xv.y - sn * yv.y);
+            y[r] = make_double2(sn * xv.x + cs * yv.x, sn * xv.y + cs * yv.y);
+          }
+        }
+        for (int r = tid + kRegRows * kThreads; r < nr; r += kThreads) {
           const double2 xv = x[r], yv = cmul(e, y[r]);
           x[r] = make_double2(cs * xv.x - sn * yv.x, cs * xv.y - sn * yv.y);
           y[r] = make_double2(sn * xv.x + cs * yv.x, sn * xv.y + cs * yv.y);
         }
-        double2* vx = V + (int64_t)i * nc;
-        double2* vy = V + (int64_t)j * nc;
-        for (int r = tid; r < nc; r += kThreads) {
+#pragma unroll
+        for (int q = 0; q < kRegV; ++q) {
+          const int r = tid + q * kThreads;
+          if (r < nc) {
+            const double2 xv = vxr[q], yv = cmul(e, vyr[q]);
+            vx[r] = make_double2(cs * xv.x - sn * yv.x, cs * xv.y - sn * yv.y);
+            vy[r] = make_double2(sn * xv.x + cs * yv.x, sn * xv.y + cs * yv.y);
+          }
+        }
+        for (int r = tid + kRegV * kThreads; r < nc; r += kThreads) {
           const double2 xv = vx[r], yv = cmul(e, vy[r]);
           vx[r] = make_double2(cs * xv.x - sn * yv.x, cs * xv.y - sn * yv.y);
           vy[r] = make_double2(sn * xv.x + cs * yv.x, sn * xv.y + cs * yv.y);
@@ -228,7 +300,7 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_grid(double2* __restrict__ 
       // the sweep's rotation count is published before its last barrier
       if (rd == N - 2 && tid == 0 && rot > 0) atomicAdd(sync + kBarLanes + sweep, rot);
       ++nbar;
-      ok = grid_sync(sync, nbar * (unsigned)G, wait_ns, flag);
+      ok = phase_sync<kCluster>(sync, nbar * (unsigned)G, wait_ns, flag);
     }
     if (!ok) break;
     if (tid == 0) s_total = ld_acquire(sync + kBarLanes + sweep);
@@ -259,6 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_grid(double2* __restrict__ 
 
 struct GridInfo {
   int sms = 0, coop = 0, occ = 0;
+  bool cluster16 = false;
 };
 GridInfo grid_info() {
   static std::once_flag once;
@@ -268,7 +341,10 @@ GridInfo grid_info() {
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&gi.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       gi.sms = 1;
     if (cudaDeviceGetAttribute(&gi.coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) gi.coop = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gi.occ, k_jacobi_grid, kThreads, 0) != cudaSuccess) gi.occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gi.occ, k_jacobi_grid<false>, kThreads, 0) != cudaSuccess)
+      gi.occ = 0;
+    gi.cluster16 = cudaFuncSetAttribute(k_jacobi_grid<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                   cudaSuccess;
   });
   return gi;
 }
@@ -284,26 +360,36 @@ bool launch_jacobi_svd_grid(const double2* theta, int m, int n, double2* A, doub
                             unsigned* sync, int* flag, uint64_t wait_ns, cudaStream_t s) {
   const int nc = std::min(m, n), nr = std::max(m, n);
   const GridInfo gi = grid_info();
-  if (nc < kJacGridMinCols || !gi.coop || gi.occ < 1) {
+  const int npairs = (nc + 1) / 2;
+  const bool cluster = npairs <= (gi.cluster16 ? kJacClusterMax : 8);
+  if (nc <= kJacOneCtaMaxCols || (!cluster && (!gi.coop || gi.occ < 1))) {
     launch_jacobi_svd(theta, m, n, A, V, sigma, info, s);
     return cudaGetLastError() == cudaSuccess;
   }
   const int64_t tot = (int64_t)nr * nc + (int64_t)nc * nc;
   k_svd_load<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, s>>>(theta, m, n, A, V);
   if (cudaMemsetAsync(sync, 0, kSvdSyncInts * sizeof(unsigned), s) != cudaSuccess) return false;
-  const int npairs = (nc + 1) / 2;
-  const int G = std::max(1, std::min(npairs, gi.sms * std::min(gi.occ, 2)));
+  const int tr = n > m ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(G, 1, 1);
   cfg.blockDim = dim3(kThreads, 1, 1);
   cfg.stream = s;
   cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeCooperative;
-  at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  const int tr = n > m ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k_jacobi_grid, A, V, nr, nc, sigma, info, sync, flag, jacobi_tol(m, n),
+  if (cluster) {  // one pair per CTA, the CTAs one cluster
+    cfg.gridDim = dim3(npairs, 1, 1);
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = npairs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    return cudaLaunchKernelEx(&cfg, k_jacobi_grid<true>, A, V, nr, nc, sigma, info, sync, flag, jacobi_tol(m, n),
+                              kJacMaxSweeps, tr, wait_ns) == cudaSuccess;
+  }
+  const int G = std::max(1, std::min(npairs, gi.sms * std::min(gi.occ, 2)));
+  cfg.gridDim = dim3(G, 1, 1);
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  return cudaLaunchKernelEx(&cfg, k_jacobi_grid<false>, A, V, nr, nc, sigma, info, sync, flag, jacobi_tol(m, n),
                             kJacMaxSweeps, tr, wait_ns) == cudaSuccess;
 }
 

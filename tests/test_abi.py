@@ -88,7 +88,8 @@ def test_params_round_trip_and_range_checks(lib):
     assert lib.ttn_get_params(h, C.byref(p)) == 0
     assert (p.qr_tol, p.kappa, p.max_rank, p.max_split, p.tensor_cores) == (1e-9, 2.5, 32, 8, 1)
     for field, bad in (("max_split", 0), ("max_split", 9), ("kappa", 0.0), ("ps2_ratio", 0.5), ("max_rank", 0),
-                       ("tensor_cores", 3), ("tensor_cores", -1), ("wait_s", -1.0), ("wait_s", 61.0)):
+                       ("tensor_cores", 3), ("tensor_cores", -1), ("wait_s", -1.0), ("wait_s", 61.0),
+                       ("tile_warps", 3), ("tile_warps", 16), ("tile_warps", -1)):
         q = _lib.ttn_params()
         C.memmove(C.byref(q), C.byref(p), C.sizeof(p))
         setattr(q, field, bad)
@@ -98,6 +99,65 @@ def test_params_round_trip_and_range_checks(lib):
     assert _load(lib, h, heom.heom_sop(w.H, w.baths, w.depth)) == 0
     q = _lib.ttn_params()
     assert lib.ttn_get_params(h, C.byref(q)) == 0 and q.max_split == 1
+    lib.ttn_destroy(h)
+
+
+def _tuning_rows(lib, h):
+    from paper_2603_17711_gb300 import _lib
+    n = C.c_int32()
+    assert lib.ttn_tuning_get(h, None, 0, C.byref(n)) == 0
+    rows = np.zeros((n.value, _lib.TTN_TUNING_COLS), np.int32)
+    assert lib.ttn_tuning_get(h, rows.ctypes.data_as(C.POINTER(C.c_int32)), n.value, C.byref(n)) == 0
+    return rows
+
+
+def test_tile_shapes_rows_round_trip(lib):
+    """Tile-shape rows (the autotuner's cache format): the planned shapes,
+    tile_warps forcing the warps of every contraction list, rows applied by
+    key, and out-of-range rows refused before anything is set."""
+    from paper_2603_17711_gb300 import _lib, heom
+    w = W.exciton_chain(n_sites=3, rank=6, depth=4)
+    st, h = _create(lib, w)
+    assert st == 0
+    n = C.c_int32()
+    assert lib.ttn_tuning_get(h, None, 0, C.byref(n)) == 6  # TTN_ESTATE before sop_load
+    assert _load(lib, h, heom.heom_sop(w.H, w.baths, w.depth)) == 0
+    rows = _tuning_rows(lib, h)
+    assert len(rows) > 0 and set(rows[:, 0]) == {0, 1}
+    assert np.all(rows[:, 9] == 8) and np.all(rows[:, 10] >= 1) and np.all(rows[:, 10] <= 8)
+    ap = rows[:, 0] == 0
+    assert np.all(rows[ap, 7] > 0) and np.all(rows[~ap, 7] == 0)  # terms of contractions; none for projections
+    # tile_warps = 2 gives every contraction list two warps per CTA
+    p = _lib.ttn_params()
+    assert lib.ttn_get_params(h, C.byref(p)) == 0
+    p.tile_warps = 2
+    assert lib.ttn_set_params(h, C.byref(p)) == 0
+    r2 = _tuning_rows(lib, h)
+    assert np.all(r2[ap, 9] == 2) and np.all(r2[~ap, 9] == 8)
+    assert np.array_equal(r2[:, :9], rows[:, :9])
+    # rows applied by key: every list matches its own row
+    want = rows.copy()
+    want[ap, 9] = 4
+    want[:, 10] = 1
+    applied = C.c_int32()
+    assert lib.ttn_tuning_set(h, want.ctypes.data_as(C.POINTER(C.c_int32)), len(want), C.byref(applied)) == 0
+    assert applied.value == len(want)
+    assert np.array_equal(_tuning_rows(lib, h), want)
+    # a row with an unknown key sets nothing; a bad shape is refused and nothing changes
+    other = want[:1].copy()
+    other[0, 8] += 1000
+    other[0, 9] = 2
+    assert lib.ttn_tuning_set(h, other.ctypes.data_as(C.POINTER(C.c_int32)), 1, C.byref(applied)) == 0
+    assert applied.value == 0
+    for col, bad in ((9, 3), (9, 16), (10, 0), (10, 9)):
+        b = want.copy()
+        b[-1, col] = bad
+        assert lib.ttn_tuning_set(h, b.ctypes.data_as(C.POINTER(C.c_int32)), len(b), C.byref(applied)) == 1
+    b = want.copy()
+    b[~ap, 9] = 4  # projections keep 8 warps
+    if (~ap).any():
+        assert lib.ttn_tuning_set(h, b.ctypes.data_as(C.POINTER(C.c_int32)), len(b), C.byref(applied)) == 1
+    assert np.array_equal(_tuning_rows(lib, h), want)
     lib.ttn_destroy(h)
 
 
