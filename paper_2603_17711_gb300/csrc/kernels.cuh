@@ -189,23 +189,24 @@ constexpr int kJacMaxSweeps = 60;
 // Otherwise the complex rotation
 //     x' = cs x - sn e y,   y' = sn x + cs e y,   e = conj(c) / |c|
 // makes the pair orthogonal; t = sn / cs is the root of smaller modulus of
-// t^2 + 2 zeta t - 1 = 0, zeta = (b - a) / (2 |c|), written without zeta:
-//     t = sign(b - a) 2|c| / (|b - a| + sqrt((b - a)^2 + 4 |c|^2)),
-//     cs = 1 / sqrt(1 + t^2),   sn = t cs.
-// Both square roots are independent, then both quotients (t and 1/|c|), so
-// the dependent chain is square root, quotient, reciprocal square root.
+// t^2 + 2 zeta t - 1 = 0, zeta = (b - a) / (2 |c|), i.e. with d = b - a,
+//     r = sqrt(d^2 + 4 |c|^2),  u = |d| + r,  t = sign(d) 2|c| / u,
+// and cs = 1 / sqrt(1 + t^2) = u w, sn = t cs = sign(d) 2|c| w with
+// w = 1 / sqrt(u^2 + 4 |c|^2): no quotient, and the dependent chain is one
+// square root and one reciprocal square root (1/|c| is taken beside r).
 __device__ __forceinline__ bool jacobi_rotation(double a, double b, double cr, double ci, double tol, double tiny2,
                                                 double& cs, double& sn, double2& e) {
   const double c2 = cr * cr + ci * ci;
   if (!(c2 > tol * tol * a * b) || c2 == 0.0 || !(fmin(a, b) > tiny2)) return false;
   const double d = b - a;
-  const double s1 = sqrt(c2);
-  const double s2 = sqrt(fma(d, d, 4.0 * c2));
-  const double t = (d >= 0.0 ? 2.0 * s1 : -2.0 * s1) / (fabs(d) + s2);
-  const double inv = 1.0 / s1;
-  cs = rsqrt(fma(t, t, 1.0));
-  sn = t * cs;
-  e = make_double2(cr * inv, -ci * inv);
+  const double ic = rsqrt(c2);  // 1 / |c|
+  const double r = sqrt(fma(d, d, 4.0 * c2));
+  const double u = fabs(d) + r;
+  const double w = rsqrt(fma(u, u, 4.0 * c2));
+  const double ac2 = 2.0 * (c2 * ic);  // 2 |c|
+  cs = u * w;
+  sn = d >= 0.0 ? ac2 * w : -ac2 * w;
+  e = make_double2(cr * ic, -ci * ic);
   return true;
 }
 

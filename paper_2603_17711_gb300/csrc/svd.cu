@@ -52,9 +52,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kRegRows = 4;  // rows of a pair's columns a thread keeps in registers (nr <= 1024 entirely)
-constexpr int kRegV = 2;     // rows of the pair's V columns a thread keeps in registers (nc <= 512 entirely)
-static_assert(kWarps * 4 == 32, "warp 0 adds four sums of each of the eight warps, one per lane");
 constexpr int kBarLanes = 8;
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -163,6 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_grid(double2* __restrict__ 
                                                           int nc, double* __restrict__ sigma, int* __restrict__ info,
                                                           unsigned* sync, int* flag, double tol, int max_sweeps,
                                                           int tr, uint64_t wait_ns) {
+  static_assert(kWarps * 4 == 32, "warp 0 adds four sums of each warp, one per lane");
   __shared__ double s_red[kWarps][4];
   __shared__ double s_par[4];
   __shared__ int s_go;
@@ -204,45 +202,13 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_grid(double2* __restrict__ 
         if (j >= nc) continue;  // the dummy column of an odd count
         double2* x = A + (int64_t)i * nr;
         double2* y = A + (int64_t)j * nr;
-        double2* vx = V + (int64_t)i * nc;
-        double2* vy = V + (int64_t)j * nc;
-        // the pair's first kRegRows rows per thread of x, y and of the V columns
-        // stay in registers from the Gram sums to the update; the V loads are
-        // issued first so that their latency hides behind the sums
-        double2 xr[kRegRows], yr[kRegRows], vxr[kRegV], vyr[kRegV];
-#pragma unroll
-        for (int q = 0; q < kRegV; ++q) {
-          const int r = tid + q * kThreads;
-          if (r < nc) {
-            vxr[q] = vx[r];
-            vyr[q] = vy[r];
-          }
-        }
         double a = 0.0, b = 0.0, cr = 0.0, ci = 0.0;
-#pragma unroll
-        for (int q = 0; q < kRegRows; ++q) {
-          const int r = tid + q * kThreads;
-          if (r < nr) {
-            xr[q] = x[r];
-            yr[q] = y[r];
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < kRegRows; ++q) {
-          if (tid + q * kThreads < nr) {
-            const double2 xv = xr[q], yv = yr[q];
-            a = fma(xv.x, xv.x, fma(xv.y, xv.y, a));
-            b = fma(yv.x, yv.x, fma(yv.y, yv.y, b));
-            cr = fma(xv.x, yv.x, fma(xv.y, yv.y, cr));  // Re conj(x) y
-            ci = fma(xv.x, yv.y, fma(-xv.y, yv.x, ci));  // Im conj(x) y
-          }
-        }
-        for (int r = tid + kRegRows * kThreads; r < nr; r += kThreads) {
+        for (int r = tid; r < nr; r += kThreads) {
           const double2 xv = x[r], yv = y[r];
           a = fma(xv.x, xv.x, fma(xv.y, xv.y, a));
           b = fma(yv.x, yv.x, fma(yv.y, yv.y, b));
-          cr = fma(xv.x, yv.x, fma(xv.y, yv.y, cr));
-          ci = fma(xv.x, yv.y, fma(-xv.y, yv.x, ci));
+          cr = fma(xv.x, yv.x, fma(xv.y, yv.y, cr));  // Re conj(x) y
+          ci = fma(xv.x, yv.y, fma(-xv.y, yv.x, ci));  // Im conj(x) y
         }
         const double sum = warp_sum4(a, b, cr, ci);
         if ((lane & 7) == 0) s_red[wid][lane >> 3] = sum;
@@ -267,30 +233,14 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_grid(double2* __restrict__ 
         if (!s_go) continue;
         const double cs = s_par[0], sn = s_par[1];
         const double2 e = make_double2(s_par[2], s_par[3]);
-#pragma unroll
-        for (int q = 0; q < kRegRows; ++q) {
-          const int r = tid + q * kThreads;
-          if (r < nr) {
-            const double2 xv = xr[q], yv = cmul(e, yr[q]);
-            x[r] = make_double2(cs * xv.x - sn * yv.x, cs * xv.y - sn * yv.y);
-            y[r] = make_double2(sn * xv.x + cs * yv.x, sn * xv.y + cs * yv.y);
-          }
-        }
-        for (int r = tid + kRegRows * kThreads; r < nr; r += kThreads) {
+        for (int r = tid; r < nr; r += kThreads) {
           const double2 xv = x[r], yv = cmul(e, y[r]);
           x[r] = make_double2(cs * xv.x - sn * yv.x, cs * xv.y - sn * yv.y);
           y[r] = make_double2(sn * xv.x + cs * yv.x, sn * xv.y + cs * yv.y);
         }
-#pragma unroll
-        for (int q = 0; q < kRegV; ++q) {
-          const int r = tid + q * kThreads;
-          if (r < nc) {
-            const double2 xv = vxr[q], yv = cmul(e, vyr[q]);
-            vx[r] = make_double2(cs * xv.x - sn * yv.x, cs * xv.y - sn * yv.y);
-            vy[r] = make_double2(sn * xv.x + cs * yv.x, sn * xv.y + cs * yv.y);
-          }
-        }
-        for (int r = tid + kRegV * kThreads; r < nc; r += kThreads) {
+        double2* vx = V + (int64_t)i * nc;
+        double2* vy = V + (int64_t)j * nc;
+        for (int r = tid; r < nc; r += kThreads) {
           const double2 xv = vx[r], yv = cmul(e, vy[r]);
           vx[r] = make_double2(cs * xv.x - sn * yv.x, cs * xv.y - sn * yv.y);
           vy[r] = make_double2(sn * xv.x + cs * yv.x, sn * xv.y + cs * yv.y);
@@ -361,7 +311,7 @@ bool launch_jacobi_svd_grid(const double2* theta, int m, int n, double2* A, doub
   const int nc = std::min(m, n), nr = std::max(m, n);
   const GridInfo gi = grid_info();
   const int npairs = (nc + 1) / 2;
-  const bool cluster = npairs <= (gi.cluster16 ? kJacClusterMax : 8);
+  const bool cluster = npairs <= (gi.cluster16 ? kJacClusterMax : 8);  // one pair per CTA, one cluster
   if (nc <= kJacOneCtaMaxCols || (!cluster && (!gi.coop || gi.occ < 1))) {
     launch_jacobi_svd(theta, m, n, A, V, sigma, info, s);
     return cudaGetLastError() == cudaSuccess;
@@ -370,6 +320,7 @@ bool launch_jacobi_svd_grid(const double2* theta, int m, int n, double2* A, doub
   k_svd_load<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, s>>>(theta, m, n, A, V);
   if (cudaMemsetAsync(sync, 0, kSvdSyncInts * sizeof(unsigned), s) != cudaSuccess) return false;
   const int tr = n > m ? 1 : 0;
+  const double tol = jacobi_tol(m, n);
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(kThreads, 1, 1);
   cfg.stream = s;
@@ -382,15 +333,15 @@ bool launch_jacobi_svd_grid(const double2* theta, int m, int n, double2* A, doub
     at[0].val.clusterDim.x = npairs;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
-    return cudaLaunchKernelEx(&cfg, k_jacobi_grid<true>, A, V, nr, nc, sigma, info, sync, flag, jacobi_tol(m, n),
-                              kJacMaxSweeps, tr, wait_ns) == cudaSuccess;
+    return cudaLaunchKernelEx(&cfg, k_jacobi_grid<true>, A, V, nr, nc, sigma, info, sync, flag, tol, kJacMaxSweeps, tr,
+                              wait_ns) == cudaSuccess;
   }
   const int G = std::max(1, std::min(npairs, gi.sms * std::min(gi.occ, 2)));
   cfg.gridDim = dim3(G, 1, 1);
   at[0].id = cudaLaunchAttributeCooperative;
   at[0].val.cooperative = 1;
-  return cudaLaunchKernelEx(&cfg, k_jacobi_grid<false>, A, V, nr, nc, sigma, info, sync, flag, jacobi_tol(m, n),
-                            kJacMaxSweeps, tr, wait_ns) == cudaSuccess;
+  return cudaLaunchKernelEx(&cfg, k_jacobi_grid<false>, A, V, nr, nc, sigma, info, sync, flag, tol, kJacMaxSweeps, tr,
+                            wait_ns) == cudaSuccess;
 }
 
 namespace {

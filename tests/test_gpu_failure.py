@@ -46,16 +46,32 @@ def test_grid_panel_qr_zero_wait_then_fresh_handle(pkg):
 
 
 def test_grid_jacobi_zero_wait_in_ps2_then_fresh_handle(pkg):
-    w = W.driven_structured_tls(n_pade=1, depth=10, cap=32)
-    params = {"max_rank": 32, "ps2_atol": 1e-6, "wait_s": 0.0}
-    g = pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0, drives=w.drives,
-                       params=params)
+    # bonds of rank 23 between internal nodes give two-site matrices of 368 x 207,
+    # whose Jacobi SVD runs over the whole GPU with one grid barrier per round; the
+    # column count is odd, so one CTA holds the dummy pair of every round and
+    # reaches the barrier first, where a zero wait gives up at its first poll
+    wc = W.exciton_chain(n_sites=3, rank=23, depth=4)
+    g = pkg.from_model(wc.H, wc.baths, wc.depth, wc.parent, wc.leg_node, wc.ranks, rho0=wc.rho0,
+                       params={"max_rank": 32, "ps2_atol": 1e-6, "wait_s": 0.0})
+    # a generic state (random isometries below a random root): from the product
+    # state ps2 would cut every bond to a few directions before the wide pairs
+    rng = np.random.default_rng(23)
+    for u in range(len(wc.parent)):
+        d0, d1, d2 = g.ttn_node_shape(u)
+        if u == 0:
+            t = rng.normal(size=(d0, d1, d2)) + 1j * rng.normal(size=(d0, d1, d2))
+            t /= np.linalg.norm(t)
+        else:
+            q = np.linalg.qr(rng.normal(size=(d1 * d2, d0)) + 1j * rng.normal(size=(d1 * d2, d0)))[0]
+            t = q.T.reshape(d0, d1, d2)  # t[a, b, c] = q[(b, c), a]: orthonormal toward the parent
+        g.ttn_set_node(u, t)
     with pytest.raises(pkg.TTNError) as e:
-        for _ in range(20):  # the two-site matrices reach 24 columns within a few steps
-            g.ttn_step(w.dt, pkg.TTN_PS2, 1)
+        for _ in range(3):
+            g.ttn_step(wc.dt, pkg.TTN_PS2, 1)
     assert e.value.status == TTN_ETIMEOUT
     g.close()
-    params["wait_s"] = 2.0
+    w = W.driven_structured_tls(n_pade=1, depth=10, cap=32)
+    params = {"max_rank": 32, "ps2_atol": 1e-6, "wait_s": 2.0}
     g = pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0, drives=w.drives,
                        params=params)
     o = ottn.from_workload(w, params=ottn.Params(ps2_atol=1e-6, max_rank=32))
