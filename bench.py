@@ -45,7 +45,7 @@ METRIC = "HEOM-TTN steps/s & node-contraction TFLOP/s vs plain FP64 at RDM err <
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2 FP64 FMA/clk/SM x ~2.07 GHz)
 WORKLOAD = "7-site Frenkel exciton chain, 21 features (1 Drude + 2 Pade per site), depth 8, BTT, rank 20, ps1, dt 0.05 fs"
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-APPLY_DRAM_BYTES = 139524   # ncu: mean DRAM bytes (read + write) per k_apply launch of one timed step
+APPLY_DRAM_BYTES = 237296   # ncu: mean DRAM bytes (read + write) per k_apply launch of one timed step
 
 
 def workload():
@@ -736,7 +736,8 @@ def bench_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved,
                      "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                      "traffic": APPLY_DRAM_BYTES if names[dom].startswith("node/bond") else None,
-                     "traffic_source": "mean dram__bytes_read+write per k_apply launch, ncu capture of 60 launches "
+                     "traffic_source": "mean dram__bytes_read+write per k_apply launch over the 857 launches of one "
+                                       "timed step, ncu (1 pass; caches flushed before each launch) "
                                        "(profiles/apply_traffic_exciton7_r20_fp64.md)",
                      "peak_source": "FP64 torch.matmul 4096^3 measured in this run (peaks.fp64_tflops); "
                                     "nominal FP64 is %.2f" % FP64_PEAK_TFLOPS,

@@ -425,6 +425,9 @@ ttn_status ttn_svd(const void* a_dev, int32_t m, int32_t n, void* u_dev, double*
                    void* ws_dev, size_t ws_bytes, double wait_s, int32_t* sweeps_out, void* stream);
 
 const char* ttn_last_error(ttn_t h);
+/* Waits for the work queued on the handle's stream (a step that failed part-way
+ * may have left launches behind), then frees the handle's host resources,
+ * graphs and events. The caller frees the workspace afterwards. */
 void ttn_destroy(ttn_t h);
 
 #ifdef __cplusplus

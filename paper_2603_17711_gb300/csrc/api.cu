@@ -166,6 +166,10 @@ struct ttn_ctx {
   }
 
   ~ttn_ctx() {
+    // the caller frees the workspace once ttn_destroy returns: nothing queued on
+    // the handle's stream may still touch it (a step that failed part-way can
+    // leave launches behind)
+    if (stream) cudaStreamSynchronize(stream);
     drop_batch();
     drop_graph();
     for (auto& m : marks) {
@@ -368,6 +372,7 @@ struct Exec {
   // with CUDA events on the handle's stream
   template <typename F>
   void run(int kind, double flops, F&& launch) {
+    if (err != cudaSuccess || fail_st != TTN_OK) return;  // a failed step launches nothing more
     h->n_launch[kind] += 1;
     h->n_flops[kind] += flops;
     if (h->prof_mode == 0) {
@@ -1460,6 +1465,7 @@ ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
       Exec ex(h);
       for (int k = 0; k < n_steps; ++k) {
         ex.step_ps2(dt, h->t);
+        if (ex.err != cudaSuccess || ex.fail_st != TTN_OK) cudaStreamSynchronize(h->stream);  // drain what was issued
         if (ex.err != cudaSuccess) return cuda_fail(h, ex.err, "ps2 step");
         if (ex.fail_st != TTN_OK) return h->fail(ex.fail_st, ex.fail_msg);
         h->t += dt;

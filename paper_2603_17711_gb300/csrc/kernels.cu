@@ -145,9 +145,7 @@ __device__ __forceinline__ typename Cx<R>::T tile_sum(const DevTables& T, const 
   using C = Cx<R>;
   using V = typename C::T;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int o = L.out_begin;
-  while (o + 1 < L.out_end && T.outs[o + 1].tile0 <= tile) ++o;
-  out = T.outs[o];
+  out = T.outs[list_output(T.outs, L.out_begin, L.out_end, L.tpo, tile)];
   Geo g;
   g.d0 = out.d0; g.d1 = out.d1; g.d2 = out.d2; g.d3 = out.d3;
   g.s2 = g.d3;
@@ -300,9 +298,7 @@ __global__ void __launch_bounds__(32 * kPjWarps, 4) k_project(DevTables T, PjLis
   const int K = L.k;
   const int tile = blockIdx.x / K, rank = blockIdx.x % K;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int o = L.out_begin;
-  while (o + 1 < L.out_end && T.pjs[o + 1].tile0 <= tile) ++o;
-  const PjOut pj = T.pjs[o];
+  const PjOut pj = T.pjs[list_output(T.pjs, L.out_begin, L.out_end, L.tpo, tile)];
   const int dd[3] = {pj.d0, pj.d1, pj.d2};
   const int64_t st[3] = {(int64_t)pj.d1 * pj.d2, pj.d2, 1};
   const int l = pj.leg;

@@ -24,6 +24,24 @@ struct DevTables {
   const PjOut* pjs;
 };
 
+// Output of a job list that holds output tile `tile` (tile0 ascending over the
+// list): one division when all outputs have the same number of tiles (tpo),
+// else a binary search -- a few dependent table loads instead of one per
+// earlier output.
+template <typename Out>
+__device__ __forceinline__ int list_output(const Out* outs, int out_begin, int out_end, int tpo, int tile) {
+  if (tpo > 0) return out_begin + tile / tpo;
+  int lo = out_begin, hi = out_end - 1;  // the last output with tile0 <= tile
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (outs[mid].tile0 <= tile)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 // Epilogue of the apply kernel. STORE writes each output to its dst buffer;
 // RKs (s = 1..4) fuse the classical RK4 stage update of the FP64 state y with
 // step h (k = the computed sum, acc and y in FP64, ys in the contraction type):

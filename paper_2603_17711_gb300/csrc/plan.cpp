@@ -522,7 +522,9 @@ int Plan::add_list(const std::vector<ApOut>& outs, const std::vector<std::vector
     o.term_end = (int)ap_terms.size();
     o.tile0 = tiles;
     int64_t p = (int64_t)o.d0 * o.d1 * o.d2 * o.d3;
-    tiles += (int)((p + kApTile - 1) / kApTile);
+    const int nt = (int)((p + kApTile - 1) / kApTile);
+    L.tpo = i == 0 ? nt : (L.tpo == nt ? nt : 0);
+    tiles += nt;
     ap_outs.push_back(o);
   }
   L.out_end = (int)ap_outs.size();
@@ -550,11 +552,14 @@ int Plan::add_pj_list(const std::vector<PjOut>& outs) {
   L.out_begin = (int)pj_outs.size();
   L.flops = 0;
   int tiles = 0;
-  for (PjOut o : outs) {
+  for (size_t i = 0; i < outs.size(); ++i) {
+    PjOut o = outs[i];
     o.tile0 = tiles;
     int d = o.leg == 0 ? o.d0 : o.leg == 1 ? o.d1 : o.d2;
     L.flops += 8.0 * o.d0 * o.d1 * o.d2 * d;
-    tiles += (d * d + kPjTile - 1) / kPjTile;
+    const int nt = (d * d + kPjTile - 1) / kPjTile;
+    L.tpo = i == 0 ? nt : (L.tpo == nt ? nt : 0);
+    tiles += nt;
     pj_outs.push_back(o);
   }
   L.out_end = (int)pj_outs.size();

@@ -109,6 +109,7 @@ struct ApList {
   int32_t useful = 1;  // largest split that still gives every warp work (for w warps per CTA)
   int32_t w = 8;       // warps per CTA (2, 4 or 8): with k, the tile shape of the launch
   int32_t units = 1;   // work units of the list's largest output tile
+  int32_t tpo = 0;     // tiles per output when every output has as many (tile -> output by one division), else 0
   double flops;        // algorithmic: 8 * P * d_leg per non-identity term and output
 };
 // Projection job: E[x',x] = sum_r conj(U[.. x' at leg ..]) W[.. x at leg ..].
@@ -124,6 +125,7 @@ struct PjList {
   int32_t n_tiles;
   int32_t k = 1;       // CTAs sharing one output tile (thread-block cluster size, 1..8)
   int32_t useful = 1;  // largest split that still gives every warp >= 4 positions
+  int32_t tpo = 0;     // tiles per output when every output has as many, else 0
   double flops;        // 8 * P * d_leg per output
 };
 

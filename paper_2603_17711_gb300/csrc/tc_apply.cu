@@ -540,9 +540,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
 // (RK) or the destination (store).
 __global__ void k_tc_epilogue(DevTables T, ApList L, Epi ep, const float2* acc, int nplanes, int64_t pstride) {
   const int tile = blockIdx.x;
-  int o = L.out_begin;
-  while (o + 1 < L.out_end && T.outs[o + 1].tile0 <= tile) ++o;
-  const ApOut out = T.outs[o];
+  const ApOut out = T.outs[list_output(T.outs, L.out_begin, L.out_end, L.tpo, tile)];
   const int64_t P = (int64_t)out.d0 * out.d1 * out.d2;
   const int64_t e = (int64_t)(tile - out.tile0) * kApTile + threadIdx.x;
   if (e >= P) return;
