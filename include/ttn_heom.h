@@ -395,7 +395,8 @@ ttn_status ttn_autotune(ttn_t h, int32_t reps);
  * steps of the handles (ttn_batch_step, after one untimed step that captures
  * the graphs) with tile_warps = 8, 4 and 2 on every member, keeps the fastest
  * (another must win by 3 %) and puts every member's state back (checkpoint
- * blobs in host memory), so the batch continues from where it was. The members'
+ * blobs in host memory) together with its ttn_stats counters, so the batch
+ * continues from where it was. The members'
  * lists get the planned shapes for that warp count. *warps_out (nullable): the
  * warps chosen; ms_out (nullable, 3 floats): ms per batched step for 8, 4, 2.
  * Synchronises the members' streams. Errors: as ttn_batch_step, TTN_EINVAL for

@@ -1835,8 +1835,15 @@ ttn_status ttn_batch_autotune(ttn_t* hs, int32_t n, double dt, int32_t reps, int
   ttn_t h0 = hs[0];
   return guarded(h0, [&]() -> ttn_status {
     if (!(std::isfinite(dt)) || dt <= 0) return h0->fail(TTN_EINVAL, "bad dt");
-    // every member's state, to be put back after the timed steps
+    // every member's state and statistics, to be put back after the timed steps
     std::vector<std::vector<char>> saved(n);
+    std::vector<std::array<int64_t, 4>> saved_launch(n);
+    std::vector<std::array<double, 4>> saved_flops(n);
+    for (int i = 0; i < n; ++i)
+      for (int c = 0; c < 4; ++c) {
+        saved_launch[i][c] = hs[i]->n_launch[c];
+        saved_flops[i][c] = hs[i]->n_flops[c];
+      }
     for (int i = 0; i < n; ++i) {
       size_t b = 0;
       ttn_status st = ttn_checkpoint_size(hs[i], &b);
@@ -1886,6 +1893,10 @@ ttn_status ttn_batch_autotune(ttn_t* hs, int32_t n, double dt, int32_t reps, int
     for (int i = 0; i < n && st == TTN_OK; ++i) {
       st = ttn_checkpoint_load(hs[i], saved[i].data(), saved[i].size());
       if (st != TTN_OK) return h0->fail(st, std::string("batch member: ") + hs[i]->err);
+      for (int c = 0; c < 4; ++c) {
+        hs[i]->n_launch[c] = saved_launch[i][c];
+        hs[i]->n_flops[c] = saved_flops[i][c];
+      }
     }
     if (warps_out) *warps_out = best;
     return st;

@@ -85,9 +85,11 @@ def test_batch_autotune_puts_the_states_back(pkg):
         h.ttn_set_params(max_split=1)
     t0 = [h.ttn_time() for h in hs]
     r0 = [h.ttn_rdm() for h in hs]
+    s0 = [[h.ttn_stats(k) for k in range(4)] for h in hs]
     res = pkg.ttn_batch_autotune(hs, 0.01, 1)
     assert res["warps"] in (8, 4, 2) and all(v > 0 for v in res["ms_per_batched_step"].values())
     assert [h.ttn_time() for h in hs] == t0
+    assert [[h.ttn_stats(k) for k in range(4)] for h in hs] == s0  # counters put back too
     for a, h in zip(r0, hs):
         assert np.array_equal(h.ttn_rdm(), a)
     fresh = [gpu_from(pkg, bw) for bw in ws]
