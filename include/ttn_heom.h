@@ -26,9 +26,13 @@
  *    memory itself. The caller frees the workspace after ttn_destroy.
  *  - Errors: every entry point returns a ttn_status and never aborts;
  *    ttn_last_error(h) describes the last failure. A failing call leaves the
- *    handle in the state it had before the call, except that TTN_ENUMERIC and
- *    TTN_ECUDA from ttn_step leave the state undefined (re-seed with
- *    ttn_set_rdo0 or ttn_set_node).
+ *    handle in the state it had before the call, except that TTN_ECUDA from
+ *    any call, and TTN_ENUMERIC / TTN_ETIMEOUT from ps1 steps (which run
+ *    asynchronously and report a failure at a later synchronising call),
+ *    leave the state undefined (re-seed with ttn_set_rdo0 or ttn_set_node).
+ *    ps2, vmf and mix steps run under host control: one that fails with
+ *    TTN_ETIMEOUT or TTN_ENUMERIC puts back the time, ranks and node tensors
+ *    the handle had at the start of the call.
  *  - A handle is not thread safe; distinct handles are independent.
  *  - All device work is issued on the stream given by ttn_set_stream
  *    (default: the legacy default stream). Calls that return host data
@@ -114,9 +118,10 @@ typedef struct {
  *                    global memory (the grid barriers of the Jacobi SVD and of
  *                    the blocked QR's panels over the whole GPU); a wait that
  *                    runs out is reported as TTN_ETIMEOUT by the next
- *                    synchronising call and the state is undefined (no
- *                    counterpart in the paper). The cluster QR's exchanges
- *                    keep a fixed 2 s bound.
+ *                    synchronising call (a ps2 / mix step puts its state
+ *                    back, a ps1 step leaves it undefined; no counterpart in
+ *                    the paper). The cluster QR's exchanges keep a fixed 2 s
+ *                    bound.
  *  ode_rtol  (1e-5)  vmf: relative and absolute tolerance of the dopri5
  *  ode_atol  (1e-7)  controller (Sec. 4, Table 4 defaults).
  *  vmf_atol  (1e-10) vmf: added to the diagonal of every single-hole density

@@ -1410,7 +1410,11 @@ ttn_status vmf_steps(ttn_t h, double dt, int n_steps) {
       CUDA_TRY(h, cudaStreamSynchronize(s));
       if (ex.err != cudaSuccess) return cuda_fail(h, ex.err, "vmf step");
       const double err = std::sqrt(sum / (double)std::max<int64_t>(cnt, 1));
-      const double fac = err == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * std::pow(err, -0.2)));
+      if (!std::isfinite(err) && !(hh > 1e-12 * dt))
+        return h->fail(TTN_ENUMERIC, "vmf: non-finite error estimate at the smallest step");
+      const double fac = !std::isfinite(err) ? 0.2
+                         : err == 0.0       ? 5.0
+                                            : std::min(5.0, std::max(0.2, 0.9 * std::pow(err, -0.2)));
       if (err <= 1.0) {
         t = last ? t1 : t + hh;
         ex.copy64(h->vmf_y, nodes, h->vmf_n);  // y5, already in the node buffers
@@ -1420,6 +1424,7 @@ ttn_status vmf_steps(ttn_t h, double dt, int n_steps) {
       } else {
         ++h->vmf_rej;
         h_try = hh * fac;
+        if (!(h_try > 1e-12 * dt)) return h->fail(TTN_ENUMERIC, "vmf: dopri5 step size underflow");
       }
     }
     ex.copy64(nodes, h->vmf_y, h->vmf_n);
@@ -1437,7 +1442,7 @@ ttn_status vmf_steps(ttn_t h, double dt, int n_steps) {
 
 extern "C" {
 
-ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
+static ttn_status step_impl(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
   return guarded(h, [&]() -> ttn_status {
     if (!h->ws_bound) return h->fail(TTN_ESTATE, "bind the workspace first");
     if (!(std::isfinite(dt)) || dt <= 0 || n_steps < 0) return h->fail(TTN_EINVAL, "bad dt or n_steps");
@@ -1451,7 +1456,7 @@ ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
           if (st != TTN_OK) return st;
           continue;
         }
-        ttn_status st = ttn_step(h, dt, TTN_PS2, 1);
+        ttn_status st = step_impl(h, dt, TTN_PS2, 1);
         if (st != TTN_OK) return st;
         int rmax = 0;
         for (int u = 1; u < h->plan.tree.n_nodes; ++u) rmax = std::max(rmax, h->plan.ranks[u]);
@@ -1500,6 +1505,36 @@ ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
     CUDA_TRY(h, cudaGetLastError());
     return TTN_OK;
   });
+}
+
+// ps2, vmf and mix run under host control (they synchronise at every split or
+// step attempt): a call that fails part-way with TTN_ETIMEOUT or TTN_ENUMERIC
+// puts the handle back to the state it had before the call (time, ranks and
+// node tensors from a checkpoint blob taken at its start). ps1 steps are
+// asynchronous, so their failures are reported by a later call.
+ttn_status ttn_step(ttn_t h, double dt, int32_t scheme, int32_t n_steps) {
+  if (!h) return TTN_EINVAL;
+  const bool sync_scheme = scheme == TTN_PS2 || scheme == TTN_VMF || scheme == TTN_MIX;
+  if (!sync_scheme || !h->ws_bound || !h->sop_loaded || n_steps <= 0) return step_impl(h, dt, scheme, n_steps);
+  std::vector<char> snap;
+  size_t bytes = 0;
+  if (ttn_checkpoint_size(h, &bytes) == TTN_OK) {
+    snap.resize(bytes);
+    if (ttn_checkpoint_save(h, snap.data(), bytes) != TTN_OK) snap.clear();
+  }
+  const bool mix0 = h->mix_switched;
+  const ttn_status st = step_impl(h, dt, scheme, n_steps);
+  if ((st == TTN_ETIMEOUT || st == TTN_ENUMERIC) && !snap.empty()) {
+    const std::string msg = h->err;
+    cudaStreamSynchronize(h->stream);
+    if (ttn_checkpoint_load(h, snap.data(), snap.size()) == TTN_OK) {
+      h->mix_switched = mix0;
+      h->err = msg + " (state put back to the start of the call)";
+    } else {
+      h->err = msg + " (the state could not be put back: " + h->err + ")";
+    }
+  }
+  return st;
 }
 
 static ttn_status check_flag(ttn_t h) {

@@ -51,25 +51,44 @@ def test_grid_jacobi_zero_wait_in_ps2_then_fresh_handle(pkg):
     # column count is odd, so one CTA holds the dummy pair of every round and
     # reaches the barrier first, where a zero wait gives up at its first poll
     wc = W.exciton_chain(n_sites=3, rank=23, depth=4)
+
+    def generic(g):
+        # a generic state (random isometries below a random root): from the product
+        # state ps2 would cut every bond to a few directions before the wide pairs
+        rng = np.random.default_rng(23)
+        for u in range(len(wc.parent)):
+            d0, d1, d2 = g.ttn_node_shape(u)
+            if u == 0:
+                t = rng.normal(size=(d0, d1, d2)) + 1j * rng.normal(size=(d0, d1, d2))
+                t /= np.linalg.norm(t)
+            else:
+                q = np.linalg.qr(rng.normal(size=(d1 * d2, d0)) + 1j * rng.normal(size=(d1 * d2, d0)))[0]
+                t = q.T.reshape(d0, d1, d2)  # t[a, b, c] = q[(b, c), a]: orthonormal toward the parent
+            g.ttn_set_node(u, t)
+
     g = pkg.from_model(wc.H, wc.baths, wc.depth, wc.parent, wc.leg_node, wc.ranks, rho0=wc.rho0,
                        params={"max_rank": 32, "ps2_atol": 1e-6, "wait_s": 0.0})
-    # a generic state (random isometries below a random root): from the product
-    # state ps2 would cut every bond to a few directions before the wide pairs
-    rng = np.random.default_rng(23)
-    for u in range(len(wc.parent)):
-        d0, d1, d2 = g.ttn_node_shape(u)
-        if u == 0:
-            t = rng.normal(size=(d0, d1, d2)) + 1j * rng.normal(size=(d0, d1, d2))
-            t /= np.linalg.norm(t)
-        else:
-            q = np.linalg.qr(rng.normal(size=(d1 * d2, d0)) + 1j * rng.normal(size=(d1 * d2, d0)))[0]
-            t = q.T.reshape(d0, d1, d2)  # t[a, b, c] = q[(b, c), a]: orthonormal toward the parent
-        g.ttn_set_node(u, t)
+    generic(g)
+    nodes0 = [g.ttn_get_node(u) for u in range(len(wc.parent))]
+    ranks0, t0 = g.ttn_get_ranks(), g.ttn_time()
     with pytest.raises(pkg.TTNError) as e:
-        for _ in range(3):
-            g.ttn_step(wc.dt, pkg.TTN_PS2, 1)
+        g.ttn_step(wc.dt, pkg.TTN_PS2, 1)
     assert e.value.status == TTN_ETIMEOUT
+    # the ps2 step that gave up put the handle back to the start of the call
+    assert np.array_equal(g.ttn_get_ranks(), ranks0) and g.ttn_time() == t0
+    for u in range(len(wc.parent)):
+        assert np.array_equal(g.ttn_get_node(u), nodes0[u])
+    # and it steps on exactly like a handle that never failed
+    g.ttn_set_params(wait_s=2.0)
+    g.ttn_step(wc.dt, pkg.TTN_PS2, 1)
+    g2 = pkg.from_model(wc.H, wc.baths, wc.depth, wc.parent, wc.leg_node, wc.ranks, rho0=wc.rho0,
+                        params={"max_rank": 32, "ps2_atol": 1e-6, "wait_s": 2.0})
+    generic(g2)
+    g2.ttn_step(wc.dt, pkg.TTN_PS2, 1)
+    assert np.array_equal(g.ttn_get_ranks(), g2.ttn_get_ranks())
+    assert np.array_equal(g.ttn_rdm(), g2.ttn_rdm())
     g.close()
+    g2.close()
     w = W.driven_structured_tls(n_pade=1, depth=10, cap=32)
     params = {"max_rank": 32, "ps2_atol": 1e-6, "wait_s": 2.0}
     g = pkg.from_model(w.H, w.baths, w.depth, w.parent, w.leg_node, w.ranks, rho0=w.rho0, drives=w.drives,
