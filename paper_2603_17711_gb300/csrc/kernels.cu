@@ -155,10 +155,19 @@ __device__ __forceinline__ typename Cx<R>::T tile_sum(const DevTables& T, const 
   idx = (int64_t)(tile - out.tile0) * kApTile + lane;
   V acc = C::zero();
   if (idx < P) {
-    g.i0 = (int)(idx / g.s0);
-    g.i1 = (int)((idx / g.s1) % g.d1);
-    g.i2 = (int)((idx / g.s2) % g.d2);
-    g.i3 = (int)(idx % g.d3);
+    if (P <= 0x7fffffff) {  // every tensor of these trees: 32-bit index arithmetic
+      const unsigned x = (unsigned)idx, s1 = (unsigned)g.s1, s2 = (unsigned)g.s2;
+      const unsigned q2 = x / s2, q1 = x / s1;
+      g.i0 = (int)(x / (unsigned)g.s0);
+      g.i1 = (int)(q1 % (unsigned)g.d1);
+      g.i2 = (int)(q2 % (unsigned)g.d2);
+      g.i3 = (int)(x - q2 * s2);
+    } else {
+      g.i0 = (int)(idx / g.s0);
+      g.i1 = (int)((idx / g.s1) % g.d1);
+      g.i2 = (int)((idx / g.s2) % g.d2);
+      g.i3 = (int)(idx % g.d3);
+    }
     const int W = K * NW, me = rank * NW + wid;
     int u = 0;  // index of the term's first unit in the tile's unit list
     for (int t = out.term_begin; t < out.term_end; ++t) {

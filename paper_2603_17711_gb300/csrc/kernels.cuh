@@ -24,6 +24,21 @@ struct DevTables {
   const PjOut* pjs;
 };
 
+// q = a / b and r = a - q b for a >= 0, b > 0, in 32-bit arithmetic when both
+// fit: a 64-bit integer division is a long instruction sequence on the GPU,
+// and index decompositions sit in the inner loops of the gather, scatter and
+// contraction kernels.
+__device__ __forceinline__ int64_t idivmod(int64_t a, int64_t b, int64_t& r) {
+  if (((a | b) >> 31) == 0) {
+    const unsigned q = (unsigned)a / (unsigned)b;
+    r = a - (int64_t)q * b;
+    return q;
+  }
+  const int64_t q = a / b;
+  r = a - q * b;
+  return q;
+}
+
 // Output of a job list that holds output tile `tile` (tile0 ascending over the
 // list): one division when all outputs have the same number of tiles (tpo),
 // else a binary search -- a few dependent table loads instead of one per

@@ -44,10 +44,10 @@ __global__ void k_merge(const double2* Uf, int f0, int f1, int f2, int lf, const
   const int64_t n = (int64_t)fd[fa] * fd[fb] * sd[sa] * sd[sb];
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i3 = (int)(idx % sd[sb]);
-    const int i2 = (int)((idx / sd[sb]) % sd[sa]);
-    const int i1 = (int)((idx / ((int64_t)sd[sb] * sd[sa])) % fd[fb]);
-    const int i0 = (int)(idx / ((int64_t)sd[sb] * sd[sa] * fd[fb]));
+    int64_t i3, i2, i1;
+    int64_t q = idivmod(idx, sd[sb], i3);
+    q = idivmod(q, sd[sa], i2);
+    const int64_t i0 = idivmod(q, fd[fb], i1);
     const double2* pf = Uf + i0 * fs[fa] + i1 * fs[fb];
     const double2* ps = Us + i2 * ss[sa] + i3 * ss[sb];
     double2 acc = make_double2(0.0, 0.0);

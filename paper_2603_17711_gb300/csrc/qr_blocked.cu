@@ -111,8 +111,10 @@ __global__ void __launch_bounds__(256) k_qb_gather(const double2* U, int d0, int
   const int la = leg == 0 ? 1 : 0, lb = leg == 2 ? 1 : 2;
   double ss = 0.0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m * n; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = k / m, r = k % m;
-    const double2 v = U[c * st[leg] + (r / dd[lb]) * st[la] + (r % dd[lb]) * st[lb]];
+    int64_t r, rb;
+    const int64_t c = idivmod(k, m, r);
+    const int64_t ra = idivmod(r, dd[lb], rb);
+    const double2 v = U[c * st[leg] + ra * st[la] + rb * st[lb]];
     Acm[k] = v;
     ss = fma(v.x, v.x, fma(v.y, v.y, ss));
   }
@@ -485,7 +487,11 @@ __global__ void __launch_bounds__(256) k_qb_panel_grid(double2* A, int64_t m, in
 __global__ void k_qb_identity(double2* X, int64_t m, int64_t n, const double* sc) {
   if (aborted(sc)) return;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m * n; k += (int64_t)gridDim.x * blockDim.x)
-    X[k] = make_double2((k % m) == (k / m) ? 1.0 : 0.0, 0.0);
+  {
+    int64_t r;
+    const int64_t c = idivmod(k, m, r);
+    X[k] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+  }
 }
 
 // R (row-major n x n, row i scaled by conj(phase_i), diag alpha) and
@@ -499,7 +505,8 @@ __global__ void k_qb_finish(const double2* A, const double2* X, int64_t m, int64
   const int la = leg == 0 ? 1 : 0, lb = leg == 2 ? 1 : 2;
   const int64_t g0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
   for (int64_t k = g0; k < n * n; k += gs) {
-    const int64_t i = k / n, c = k % n;
+    int64_t c;
+    const int64_t i = idivmod(k, n, c);
     double2 v = make_double2(0.0, 0.0);
     if (c == i) {
       v = make_double2(skip[i] ? 0.0 : alpha[i], 0.0);
@@ -511,10 +518,12 @@ __global__ void k_qb_finish(const double2* A, const double2* X, int64_t m, int64
     if (R_lo) R_lo[k] = make_float2((float)v.x, (float)v.y);
   }
   for (int64_t k = g0; k < m * n; k += gs) {
-    const int64_t c = k / m, r = k % m;
+    int64_t r, rb;
+    const int64_t c = idivmod(k, m, r);
     const double2 q = X[k], p = phase[c];
     const double2 qp = make_double2(q.x * p.x - q.y * p.y, q.x * p.y + q.y * p.x);
-    const int64_t at = c * st[leg] + (r / dd[lb]) * st[la] + (r % dd[lb]) * st[lb];
+    const int64_t ra = idivmod(r, dd[lb], rb);
+    const int64_t at = c * st[leg] + ra * st[la] + rb * st[lb];
     U[at] = qp;
     if (U_lo) U_lo[at] = make_float2((float)qp.x, (float)qp.y);
   }

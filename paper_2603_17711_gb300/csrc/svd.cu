@@ -131,11 +131,14 @@ __global__ void k_svd_load(const double2* __restrict__ theta, int m, int n, doub
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < na + nv;
        k += (int64_t)gridDim.x * blockDim.x) {
     if (k < na) {
-      const int r = (int)(k % nr), c = (int)(k / nr);
-      A[k] = tr ? cconj(theta[(int64_t)c * n + r]) : theta[(int64_t)r * n + c];
+      int64_t r;
+      const int64_t c = idivmod(k, nr, r);
+      A[k] = tr ? cconj(theta[c * n + r]) : theta[r * n + c];
     } else {
       const int64_t kv = k - na;
-      V[kv] = make_double2((kv % nc) == (kv / nc) ? 1.0 : 0.0, 0.0);
+      int64_t rr;
+      const int64_t cc = idivmod(kv, nc, rr);
+      V[kv] = make_double2(rr == cc ? 1.0 : 0.0, 0.0);
     }
   }
 }
@@ -359,12 +362,13 @@ __global__ void k_svd_write(const double2* __restrict__ A, const double2* __rest
     const bool upart = q < nu;
     const int64_t qq = upart ? q : q - nu;
     int row, a;
+    int64_t rem;
     if (upart) {
-      row = (int)(qq / k);
-      a = (int)(qq % k);
+      row = (int)idivmod(qq, k, rem);
+      a = (int)rem;
     } else {
-      a = (int)(qq / n);
-      row = (int)(qq % n);
+      a = (int)idivmod(qq, n, rem);
+      row = (int)rem;
     }
     const int j = perm[a];
     const double sj = sigma[j];

@@ -326,8 +326,9 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply(DevTables T, ApList L, 
   {
     const int la = leg == 0 ? 1 : 0, lb = leg == 2 ? 1 : 2;
     for (int nn = tid; nn < kTcN; nn += kTcThreads) {
-      const int64_t n = n0 + nn;
-      base[nn] = (n / g.d[lb]) * g.st[la] + (n % g.d[lb]) * g.st[lb];
+      int64_t nb;
+      const int64_t na = idivmod(n0 + nn, g.d[lb], nb);
+      base[nn] = na * g.st[la] + nb * g.st[lb];
     }
   }
   __syncthreads();
@@ -662,7 +663,8 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_split(DevTables T, TcSplitJob
     const int x = x0 + 2 * xp;
     float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
     if (n < rest) {
-      const int64_t base = (n / d[lb]) * st[la] + (n % d[lb]) * st[lb];
+      int64_t nb;
+      const int64_t base = idivmod(n, d[lb], nb) * st[la] + nb * st[lb];
       if (x < dl) a = X[(int64_t)x * st[l] + base];
       if (x + 1 < dl) c = X[(int64_t)(x + 1) * st[l] + base];
     }
@@ -777,8 +779,9 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_apply_ring(DevTables T, ApLis
   {
     const int la = leg == 0 ? 1 : 0, lb = leg == 2 ? 1 : 2;
     for (int nn = tid; nn < kTcN; nn += kTcThreads) {
-      const int64_t n = n0 + nn;
-      base[nn] = (n / g.d[lb]) * g.st[la] + (n % g.d[lb]) * g.st[lb];
+      int64_t nb;
+      const int64_t na = idivmod(n0 + nn, g.d[lb], nb);
+      base[nn] = na * g.st[la] + nb * g.st[lb];
     }
   }
   float2* Y = part ? part + (planes ? (int64_t)(lg.pb[leg] + split) * pstride : 0) : (float2*)T.bufs[out.dst];

@@ -155,8 +155,8 @@ __global__ void k_vmf_dmi(double2* __restrict__ K, const double2* __restrict__ G
                           int r, int64_t nc) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)r * nc;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int a = (int)(e / nc);
-    const int64_t c = e % nc;
+    int64_t c;
+    const int a = (int)idivmod(e, nc, c);
     double2 s = K[e];
     for (int b = 0; b < r; ++b) s = cadd(s, cmul(dmi[a * r + b], G[(int64_t)b * nc + c]));
     K[e] = s;
@@ -189,8 +189,8 @@ __global__ void k_vmf_psub(double2* __restrict__ K, const double2* __restrict__ 
                            int64_t nc) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)r * nc;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int a = (int)(e / nc);
-    const int64_t c = e % nc;
+    int64_t c;
+    const int a = (int)idivmod(e, nc, c);
     double2 s = make_double2(0.0, 0.0);
     for (int b = 0; b < r; ++b) s = cadd(s, cmul(X[a * r + b], U[(int64_t)b * nc + c]));
     K[e] = make_double2(K[e].x - s.x, K[e].y - s.y);
