@@ -96,7 +96,7 @@ typedef struct {
  *  max_rank  (32)    ps2 bond-rank cap (Sec. 4, Table 4: max_auxiliary_rank).
  *  svd_tol   (1e-12) kept singular values <= svd_tol*sigma_1 are replaced by a
  *                    deterministic completion with zero weight.
- *  max_split (8)     1..8: at most this many CTAs (one thread-block cluster)
+ *  max_split (16)    1..16: at most this many CTAs (one thread-block cluster)
  *                    share one output tile of a contraction launch; launches
  *                    smaller than two CTAs per SM are split up to this factor
  *                    (no counterpart in the paper: GB300 work distribution).

@@ -1106,6 +1106,7 @@ ttn_status ttn_set_workspace(ttn_t h, void* dptr, size_t bytes) {
     if (!dptr || ((uintptr_t)dptr % kAlign) != 0) return h->fail(TTN_EINVAL, "workspace must be 256-byte aligned");
     for (int d = 0; d < h->plan.n_drives; ++d)
       if (!h->drives[d].fn) return h->fail(TTN_ESTATE, "a drive used by the SOP has no function");
+    allow_wide_splits();
     Plan& p = h->plan;
     Layout L = layout_of(p, h->prec);
     if (bytes < L.total) return h->fail(TTN_ENOMEM, "workspace smaller than ttn_workspace_size");

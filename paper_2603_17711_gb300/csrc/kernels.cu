@@ -5,6 +5,7 @@
 // a few hundred KB, environments of r x r) stays in L2 and L1.
 #include <algorithm>
 #include <cooperative_groups.h>
+#include <mutex>
 
 #include "kernels.cuh"
 
@@ -482,6 +483,25 @@ void launch_project(int prec, const DevTables& T, const PjList& L, cudaStream_t 
   else
     launch_split(k_project<double>, L.n_tiles, L.k, kPjWarps, s, T, L);
 }
+
+// Clusters of more than 8 CTAs are non-portable: allowed once per process for
+// every contraction and projection kernel, before any launch (and outside any
+// graph capture).
+void allow_wide_splits() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_apply<double, 8>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_apply<double, 4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_apply<double, 2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_apply<float, 8>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_apply<float, 4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_apply<float, 2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_project<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_project<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaGetLastError();
+  });
+}
+
 
 // ---------------------------------------------------------------------------
 // Householder QR (one CTA). A (m x n, m = P / d_leg, n = d_leg) is gathered

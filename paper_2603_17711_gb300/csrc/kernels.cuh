@@ -84,6 +84,9 @@ struct DriveArgs {
 };
 
 void launch_apply(int prec, const DevTables& T, const ApList& L, const Epi& e, cudaStream_t s);
+// Allows the contraction and projection kernels clusters of up to kMaxSplit
+// (16) CTAs; called once before the first launch.
+void allow_wide_splits();
 
 // Mixed form: the same list with its mode products on the tcgen05 tensor
 // cores (tc_apply.cu, 3xTF32). outs_host/terms_host: host copies of the job

@@ -105,7 +105,7 @@ struct ApOut {
 struct ApList {
   int32_t out_begin, out_end;  // into the global ApOut table
   int32_t n_tiles;
-  int32_t k = 1;       // CTAs sharing one output tile (thread-block cluster size, 1..8)
+  int32_t k = 1;       // CTAs sharing one output tile (thread-block cluster size, 1..16)
   int32_t useful = 1;  // largest split that still gives every warp work (for w warps per CTA)
   int32_t w = 8;       // warps per CTA (2, 4 or 8): with k, the tile shape of the launch
   int32_t units = 1;   // work units of the list's largest output tile
@@ -123,7 +123,7 @@ struct PjOut {
 struct PjList {
   int32_t out_begin, out_end;
   int32_t n_tiles;
-  int32_t k = 1;       // CTAs sharing one output tile (thread-block cluster size, 1..8)
+  int32_t k = 1;       // CTAs sharing one output tile (thread-block cluster size, 1..16)
   int32_t useful = 1;  // largest split that still gives every warp >= 4 positions
   int32_t tpo = 0;     // tiles per output when every output has as many, else 0
   double flops;        // 8 * P * d_leg per output
@@ -182,7 +182,7 @@ struct Plan {
   int r_cap_max = 1;
   int cap_rank = 32;
   int sm_count = 152;  // SMs of the device: sizes the per-tile CTA split of the job lists
-  int max_split = 8;   // upper bound of that split (ttn_params.max_split)
+  int max_split = 16;  // upper bound of that split (ttn_params.max_split; kMaxSplit below)
   int tile_warps = 0;  // warps per CTA of new apply lists (ttn_params.tile_warps; 0: kSplitWarps)
 
   // classes
@@ -251,6 +251,6 @@ constexpr int kApTile = 32;   // output elements per CTA of the apply kernel
 constexpr int kPjTile = 32;   // output entries per CTA of the projection kernel
 constexpr int kApChunk = 4;   // leg positions per work unit of the apply kernel
 constexpr int kSplitWarps = 8;  // warps per CTA of the apply / projection kernels
-constexpr int kMaxSplit = 8;    // at most this many CTAs (one cluster) share an output tile
+constexpr int kMaxSplit = 16;   // at most this many CTAs (one cluster, non-portable above 8) share an output tile
 
 }  // namespace ttn

@@ -86,8 +86,8 @@ def test_params_round_trip_and_range_checks(lib):
     assert st == 0
     p = _lib.ttn_params()
     assert lib.ttn_get_params(h, C.byref(p)) == 0
-    assert (p.qr_tol, p.kappa, p.max_rank, p.max_split, p.tensor_cores) == (1e-9, 2.5, 32, 8, 1)
-    for field, bad in (("max_split", 0), ("max_split", 9), ("kappa", 0.0), ("ps2_ratio", 0.5), ("max_rank", 0),
+    assert (p.qr_tol, p.kappa, p.max_rank, p.max_split, p.tensor_cores) == (1e-9, 2.5, 32, 16, 1)
+    for field, bad in (("max_split", 0), ("max_split", 17), ("kappa", 0.0), ("ps2_ratio", 0.5), ("max_rank", 0),
                        ("tensor_cores", 3), ("tensor_cores", -1), ("wait_s", -1.0), ("wait_s", 61.0),
                        ("tile_warps", 3), ("tile_warps", 16), ("tile_warps", -1)):
         q = _lib.ttn_params()
@@ -124,7 +124,7 @@ def test_tile_shapes_rows_round_trip(lib):
     assert _load(lib, h, heom.heom_sop(w.H, w.baths, w.depth)) == 0
     rows = _tuning_rows(lib, h)
     assert len(rows) > 0 and set(rows[:, 0]) == {0, 1}
-    assert np.all(rows[:, 9] == 8) and np.all(rows[:, 10] >= 1) and np.all(rows[:, 10] <= 8)
+    assert np.all(rows[:, 9] == 8) and np.all(rows[:, 10] >= 1) and np.all(rows[:, 10] <= 16)
     ap = rows[:, 0] == 0
     assert np.all(rows[ap, 7] > 0) and np.all(rows[~ap, 7] == 0)  # terms of contractions; none for projections
     # tile_warps = 2 gives every contraction list two warps per CTA
@@ -149,7 +149,7 @@ def test_tile_shapes_rows_round_trip(lib):
     other[0, 9] = 2
     assert lib.ttn_tuning_set(h, other.ctypes.data_as(C.POINTER(C.c_int32)), 1, C.byref(applied)) == 0
     assert applied.value == 0
-    for col, bad in ((9, 3), (9, 16), (10, 0), (10, 9)):
+    for col, bad in ((9, 3), (9, 16), (10, 0), (10, 17)):
         b = want.copy()
         b[-1, col] = bad
         assert lib.ttn_tuning_set(h, b.ctypes.data_as(C.POINTER(C.c_int32)), len(b), C.byref(applied)) == 1
