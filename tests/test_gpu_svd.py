@@ -37,9 +37,12 @@ def _check(pkg, A, tol=1e-13):
     return sweeps
 
 
-# one CTA up to 16 columns, one thread-block cluster for 17..32, the whole GPU beyond
+# one CTA up to 16 columns, one thread-block cluster for 17..32 (also with
+# many rows, and a wide matrix taken through its conjugate transpose), the
+# whole GPU beyond
 @pytest.mark.parametrize("m,n", [(20, 12), (12, 20), (30, 16), (33, 17), (40, 24), (24, 40), (50, 32), (200, 33),
-                                 (64, 64), (100, 37), (37, 100), (300, 120), (144, 100), (600, 71)])
+                                 (4000, 20), (31, 1500), (64, 64), (100, 37), (37, 100), (300, 120), (144, 100),
+                                 (600, 71)])
 def test_svd_matches_lapack(pkg, m, n):
     rng = np.random.default_rng(m * 1000 + n)
     sweeps = _check(pkg, _rand(rng, m, n))
